@@ -1,0 +1,152 @@
+"""Pins of the oracle's march (Eqs. MOTInversion, PnMOT), PDSA (Eq. Dn), excitation
+(Eq. E) and the FIR taps (Eqs. FIR2-4, RegReq1)."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import excitation, kernel_table, march, pdsa
+from oracle.spline import num_lags
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _small(N, eps, taps=None, steps=64, k_hat=(0, 0, 1), p_hat=(1, 0, 0)):
+    eps_r = wl.cube(N, eps)
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, ell + 1)
+    pulse = wl.pulse(N, eps, k_hat, p_hat)
+    E = excitation.tested_excitation(eps_r, pulse, steps)
+    taps = np.zeros(0) if taps is None else taps
+    return eps_r, G, E, taps, ell
+
+
+def test_march_solves_its_system(cube8_oracle):
+    """sum_{l=0}^{ell} Z_l J_{n-l} = E_n for every step (the definition)."""
+    o = cube8_oracle
+    r = march.residual(o["G"], o["cfg"]["eps_r"], o["cfg"]["taps"], o["E"][:80], o["J"][:80])
+    assert r < 1e-13
+
+
+def test_march_bounded_and_decaying(cube8_oracle):
+    """The pulse passes and the response rings down (no late-time growth)."""
+    nrm = np.sqrt((cube8_oracle["J"] ** 2).sum(axis=(1, 2)))
+    assert nrm.max() > 1.0
+    assert nrm[-32:].max() < 0.05 * nrm.max()
+
+
+def test_clausius_mossotti_single_voxel():
+    """One voxel driven by a step: the late-time current is the static response
+    3 (eps - 1)/(eps + 2) e, which follows from sum_l T = 1, sum_l K^vol = 0 and the
+    self demagnetisation -1/3 (static limit of Eq. MatrixEquation)."""
+    eps = 4.0
+    eps_r = np.full((1, 1, 1), eps)
+    ell = num_lags(1, 1, 1)
+    G, _, _ = kernel_table.octant_table(1, ell + 1)
+    chi = (eps - 1) / eps
+    e = np.array([1.0, -0.3, 0.2])
+    Nt = 400
+    E = np.broadcast_to(chi * e, (Nt, 1, 3)).copy()
+    J = march.march(G, eps_r, np.zeros(0), E)
+    assert np.abs(J[-1, 0] - 3 * (eps - 1) / (eps + 2) * e).max() < 1e-10
+
+
+def test_frequency_domain_solve_matches_transient():
+    """DFT-of-transient equals a frequency-domain solve of the same discretisation:
+    Z(z) J_N(z) = E_N(z) + tail(z), solved densely, on a damped and an undamped z."""
+    eps_r, G, E, taps, ell = _small(3, 6.0, steps=48)
+    J = march.march(G, eps_r, taps, E)
+    for z in (np.exp(0.37j), 1.05 * np.exp(2.1j), -1.0 + 0j):
+        x, JN = pdsa.frequency_identity_solve(G, eps_r, taps, E, J, z)
+        assert np.abs(x - JN).max() < 1e-10 * np.abs(JN).max()
+
+
+def test_rotation_permutes_components():
+    """A cube lit along z with x polarisation is the axis-swapped (x <-> z) image of
+    the same cube lit along x with z polarisation."""
+    N = 3
+    eps_r, G, E1, taps, _ = _small(N, 5.0, steps=40, k_hat=(0, 0, 1), p_hat=(1, 0, 0))
+    _, _, E2, _, _ = _small(N, 5.0, steps=40, k_hat=(1, 0, 0), p_hat=(0, 0, 1))
+    J1 = march.march(G, eps_r, taps, E1).reshape(40, N, N, N, 3)   # [n, w, v, u, b]
+    J2 = march.march(G, eps_r, taps, E2).reshape(40, N, N, N, 3)
+    J2s = J2.transpose(0, 3, 2, 1, 4)[..., ::-1]                      # swap x <-> z
+    assert np.abs(J1 - J2s).max() < 1e-12 * np.abs(J1).max()
+
+
+def test_linearity():
+    eps_r, G, E, taps, _ = _small(2, 3.0, steps=30)
+    rng = np.random.default_rng(3)
+    E2 = rng.normal(size=E.shape)
+    Ja = march.march(G, eps_r, taps, E)
+    Jb = march.march(G, eps_r, taps, E2)
+    Jc = march.march(G, eps_r, taps, 2.0 * E - 0.5 * E2)
+    assert np.abs(Jc - (2.0 * Ja - 0.5 * Jb)).max() < 1e-12 * np.abs(Jc).max()
+
+
+def test_z0_symmetrised_is_spd():
+    """diag(1/chi) Z_0 is symmetric positive definite (reading R4; D_0 = Z_0 of the
+    PDSA), which is what allows conjugate gradients for the per-step solve."""
+    N = 4
+    eps_r = wl.sphere(N, 12.0) * 0 + 12.0
+    eps_r[0, 0, 0] = 3.0                       # heterogeneous chi
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, 1)
+    Z0 = march.dense_Z(G, 0, eps_r, np.zeros(0))
+    e = np.repeat(eps_r.reshape(-1), 3)
+    A = Z0 / ((e - 1) / e)[:, None]
+    assert np.abs(A - A.T).max() < 1e-15
+    assert np.linalg.eigvalsh(A).min() > 0.0
+
+
+def test_pdsa_binomials_and_fir_identity():
+    """D_0 = Z_0, D_ell = sum (-1)^i Z_i, and FIR taps with sum (-1)^n delta_n = delta
+    shift D_ell by exactly delta I (Eqs. Dn, Regularization, RegReq1)."""
+    N = 2
+    eps_r = wl.cube(N, 12.0)
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, ell + 1)
+    taps = wl.fir_taps("fir3", 0.1)
+    D = pdsa.pdsa_matrices(G, eps_r, np.zeros(0), ell)
+    Dd = pdsa.pdsa_matrices(G, eps_r, taps, ell)
+    Z = [march.dense_Z(G, l, eps_r, np.zeros(0)) for l in range(ell + 1)]
+    assert np.abs(D[0] - Z[0]).max() == 0.0
+    alt = sum((-1) ** i * Z[i] for i in range(ell + 1))
+    assert np.abs(D[ell] - alt).max() < 1e-15
+    assert np.abs(Dd[ell] - D[ell] - 0.1 * np.eye(D[0].shape[0])).max() < 1e-15
+    mins = pdsa.min_eigs_symmetrised(D, eps_r)
+    assert all(m > 0 for m in mins)          # a 2^3 cube is well inside the PD regime
+
+
+def test_fir_taps_against_paper():
+    """Eqs. FIR2-FIR4 as printed (FIR4 last tap per reading R7) and Eq. RegReq1."""
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "fir_taps_paper.txt")):
+        if line.strip() and not line.startswith("#"):
+            parts = line.split()
+            rows[parts[0]] = np.array([float(v) for v in parts[1:]])
+    for k in ("fir2", "fir3", "fir4"):
+        taps = wl.fir_taps(k, 1.0)
+        assert np.array_equal(taps, rows[k])
+        assert abs(np.sum(taps * (-1.0) ** np.arange(len(taps))) - 1.0) < 1e-15
+    h = wl.fir_taps("hp9", 0.1125)
+    assert abs(np.sum(h * (-1.0) ** np.arange(9)) - 0.1125) < 1e-15
+    assert np.abs(h - h[::-1]).max() < 1e-15          # type-I linear phase
+    assert abs(h.sum()) < 1e-15                       # high-pass: no DC gain
+
+
+def test_sphere_voxelisation_tie_free():
+    for N in (8, 32, 104):
+        c = np.arange(N) + 0.5 - N / 2.0
+        r2 = c[None, None, :] ** 2 + c[None, :, None] ** 2 + c[:, None, None] ** 2
+        assert np.abs(r2 - (N / 2.0) ** 2).min() > 0.2
+    assert int((wl.sphere(32, 12.0) > 1).sum()) == 17256
+
+
+def test_excitation_quadrature_converged():
+    """Eq. E voxel average with 8 and 12 point rules agree (the pulse is smooth on the
+    voxel scale)."""
+    cfg = wl.config("cube8")
+    a = excitation.tested_excitation(cfg["eps_r"], cfg["pulse"], 4, n_first=95, npts=8)
+    b = excitation.tested_excitation(cfg["eps_r"], cfg["pulse"], 4, n_first=95, npts=12)
+    assert np.abs(a - b).max() < 1e-14 * np.abs(a).max()
