@@ -1,0 +1,201 @@
+/*
+ * mot.h - C ABI of the GB300 MOT-JVIE marching library (arXiv 2407.03323).
+ *
+ * The library marches the contrast-current-density volume integral equation in time
+ * (Sec. 2, Eqs. MOTInversion and PnMOT):
+ *
+ *     Z_0 J_n = E_n - P_{n-1},     P_{n-1} = sum_{l=1}^{ell} Z_l J_{n-l},
+ *
+ * on a uniform voxel grid, with the history P evaluated by zero-padded 3D FFTs
+ * (Sec. 3, Eq. PnFFTMOT, App. A), the FIR regularisation Z_n + delta_n I (Sec. 6.1)
+ * and a conjugate-gradient solve of the near-field operator Z_0 each step.
+ *
+ * Conventions for every call:
+ *  - Units: c0 = 1, eps0 = 1.  Voxels are cubes of edge h with c0 dt = h (the
+ *    paper's setting, Sec. 5.2); any other h/dt is rejected with MOT_ERR_ARG.
+ *  - Voxel index m = u + U (v + V w), 0-based (Sec. 2.2).  Vectors over unknowns are
+ *    "AoS": element [m][b], b = x, y, z (Eqs. CurrentVector, ExcitationVector).
+ *  - Time steps are 1-based as in the paper: the first unknown is J_1 and J_n = 0
+ *    for n <= 0 (the incident field arrives after t = 0, Sec. 2.1).
+ *  - The caller owns every buffer it passes; the library copies what it keeps and
+ *    never frees caller memory.  Pointer arguments may be host or device pointers
+ *    where stated; the library tells them apart with cudaPointerGetAttributes.
+ *  - Every call returns a mot_status.  On error, mot_last_error(ctx) returns a
+ *    message.  A context stays usable after MOT_ERR_ARG / MOT_ERR_NOT_CONVERGED /
+ *    MOT_ERR_UNSTABLE; after MOT_ERR_CUDA or MOT_ERR_TIMEOUT it is in
+ *    MOT_ERR_STATE and only mot_last_error / mot_get_info / mot_destroy work.
+ *  - Calls on one context are not thread safe; separate contexts are independent.
+ */
+#ifndef MOT_H
+#define MOT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mot_ctx mot_ctx;
+
+typedef enum {
+    MOT_OK = 0,
+    MOT_ERR_ARG = 1,            /* invalid argument (message says which)            */
+    MOT_ERR_OOM = 2,            /* device allocation failed                         */
+    MOT_ERR_CUDA = 3,           /* CUDA runtime error                               */
+    MOT_ERR_NOT_CONVERGED = 4,  /* CG did not reach its tolerance within max_iter    */
+    MOT_ERR_UNSTABLE = 5,       /* NaN/Inf or runaway growth of ||J_n|| (Sec. 5.2)   */
+    MOT_ERR_TIMEOUT = 6,        /* a device-side wait ran out of its budget          */
+    MOT_ERR_STATE = 7           /* context unusable (earlier device fault)           */
+} mot_status;
+
+typedef enum {
+    MOT_FP64 = 0,          /* every stage in FP64                                    */
+    MOT_FP32_HISTORY = 1   /* FFTs, spectra and lag MAC in FP32 with compensated
+                              accumulation; element quadrature, Z_0, FIR state and
+                              the CG solve stay FP64                                 */
+} mot_precision;
+
+typedef enum {
+    MOT_HISTORY_DIRECT = 0,  /* every lag 1..ell multiplied per step in the spatial
+                                spectral domain (Sec. 3, Eq. PnFFTMOT)                */
+    MOT_HISTORY_BLOCKED = 1  /* lags >= B by block Toeplitz products with temporal
+                                FFTs (Secs. 4-5); lags < B as in DIRECT               */
+} mot_history_scheme;
+
+/*
+ * mot_create - build a marching context (setup; not part of the per-step path).
+ *
+ * Computes ell (Eq. Ell), chi_m = (eps_m - 1)/eps_m (Eq. TDJVIE), the interaction
+ * elements G_l(d) = K^face_l(d) - delta_ab K^vol_l(d) for lags 0..ell by FP64
+ * quadrature on the GPU (Eq. Z; the element integrals are written out in
+ * the design doc), their zero-padded spatial spectra (App. A), and allocates the rings.
+ *
+ *  grid[3]   U, V, W voxels along x, y, z (each >= 1)
+ *  h[3]      voxel edges; must be equal
+ *  dt        time step; must satisfy c0 dt = h (c0 = 1)
+ *  eps_r     host pointer, U*V*W relative permittivities (>= 1), m order; copied
+ *  fir_taps  host pointer to delta_0..delta_{n_taps-1} (Z_n + delta_n I, Sec. 6.1);
+ *            may be NULL when n_taps = 0; copied
+ *  precision mot_precision
+ *  scheme    mot_history_scheme
+ *  block     block size B for MOT_HISTORY_BLOCKED (power of two, 2..ell), else 0
+ *  out       receives the context (NULL on failure)
+ * Errors: MOT_ERR_ARG, MOT_ERR_OOM, MOT_ERR_CUDA.  On failure *out is NULL and the
+ * message is available from mot_last_error(NULL).
+ */
+mot_status mot_create(const int grid[3], const double h[3], double dt,
+                      const double* eps_r, const double* fir_taps, int n_taps,
+                      int precision, int scheme, int block, mot_ctx** out);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void mot_destroy(mot_ctx* ctx);
+
+/*
+ * mot_set_excitation - stage tested excitation samples E_n (Eq. E) for the next
+ * n_steps calls-worth of steps.
+ *
+ *  n_steps   number of time steps provided (>= 1)
+ *  E         [n_steps][M][3] doubles, E_{n0+1} first where n0 is the number of steps
+ *            already marched; host or device pointer; copied into a device staging
+ *            buffer, which is reallocated if n_steps exceeds its capacity
+ *  stream    cudaStream_t to use, or NULL for the context's stream
+ * Steps without staged excitation are marched with E = 0.
+ */
+mot_status mot_set_excitation(mot_ctx* ctx, int n_steps, const double* E, void* stream);
+
+/*
+ * mot_plane_wave - tested modulated-Gaussian plane wave (Eq. E) computed on the GPU:
+ *   E^b_{m,n} = chi_m p_b (1/V) int_{V_m} sin(2 pi f_c tau) exp(-tau^2/(2 sigma_t^2)) dV,
+ *   tau = n dt - t0 - r . k_hat   (voxel m occupies [u, u+1] x [v, v+1] x [w, w+1] h).
+ *  k_hat, p_hat  unit propagation and polarisation vectors (host, 3 doubles each)
+ *  f_c, sigma_t, t0   pulse parameters in units of dt
+ *  n_first   first time index n (1-based); n_steps samples are produced
+ *  E_out     [n_steps][M][3] doubles, host or device pointer
+ */
+mot_status mot_plane_wave(mot_ctx* ctx, const double k_hat[3], const double p_hat[3],
+                          double f_c, double sigma_t, double t0, int n_first, int n_steps,
+                          double* E_out, void* stream);
+
+/*
+ * mot_march - advance the march by n_steps time steps.
+ *  J_out     [n_steps][M][3] doubles receiving J_{n0+1} .. J_{n0+n_steps} (host or
+ *            device pointer), or NULL to keep the result on the device only
+ *  stream    cudaStream_t or NULL
+ * Errors: MOT_ERR_NOT_CONVERGED (CG exceeded max_iter; J of that step is the last
+ * iterate), MOT_ERR_UNSTABLE (NaN/Inf or ||J_n|| above the growth limit; see
+ * mot_get_info for the step), MOT_ERR_CUDA.
+ */
+mot_status mot_march(mot_ctx* ctx, int n_steps, double* J_out, void* stream);
+
+/*
+ * mot_eval_history - evaluate P_{n-1} = sum_{l=1}^{ell} Z_l J_{n-l} (Eq. PnMOT,
+ * FIR taps included) for a caller-given past, through the same FFT / lag-MAC path
+ * the march uses.  The march state is reset (n0 = 0) before and after.
+ *  n_hist    number of past steps given (1..ell); older ones are zero
+ *  J_hist    [n_hist][M][3], J_{n-1} first (host or device)
+ *  P_out     [M][3] (host or device)
+ */
+mot_status mot_eval_history(mot_ctx* ctx, int n_hist, const double* J_hist, double* P_out,
+                            void* stream);
+
+/*
+ * mot_get_table - copy interaction elements G_l^{ab}(d) of lags l0..l0+n_lags-1 on
+ * the octant d in [0,U-1]x[0,V-1]x[0,W-1] to host memory.
+ *  out  host pointer, [n_lags][6][W][V][U] doubles, component order xx, yy, zz,
+ *       xy, xz, yz; other octants follow by parity (diagonal even in each d_i, the
+ *       (a, b) component odd in d_a and d_b)
+ */
+mot_status mot_get_table(mot_ctx* ctx, int l0, int n_lags, double* out);
+
+/*
+ * mot_get_spectrum - copy the spatial spectrum of lag l (1..ell) on the octant of
+ * frequencies k_i in [0, P_i/2]:  Ghat_l^{ab}(k) = sum_d G_l^{ab}(d) exp(-2 pi i k.d/P)
+ * (real by the parity of G; App. A with the circulant embedding of size P_i).
+ *  out  host pointer, [6][Pw/2+1][Pv/2+1][Pu/2+1] doubles (unnormalised)
+ */
+mot_status mot_get_spectrum(mot_ctx* ctx, int l, double* out);
+
+/* Grid facts and the last march's diagnostics.  Any pointer may be NULL.
+ *  ell, P[3]            lags and padded FFT sizes
+ *  n_done               steps marched so far
+ *  last_norm            ||J_{n_done}||_2
+ *  fail_step            step index of the first UNSTABLE/NOT_CONVERGED event, or 0
+ *  last_cg_iters        CG iterations of the last step                             */
+mot_status mot_get_info(const mot_ctx* ctx, int* ell, int P[3], int* n_done,
+                        double* last_norm, int* fail_step, int* last_cg_iters);
+
+/* Set per-step solver/monitor parameters (defaults: tol 1e-13, max_iter 200,
+ * growth_limit 1e12 times the largest norm seen).  tol is relative to ||rhs||. */
+mot_status mot_set_solver(mot_ctx* ctx, double tol, int max_iter, double growth_limit);
+
+/* Counters of mot_march calls since the last mot_set_profiling (or creation).
+ *  launches      kernels launched by mot_march
+ *  mac_launches  of which lag multiply-accumulate kernels
+ *  steps         time steps marched
+ *  cg_iters      total CG iterations
+ *  ms_*          summed CUDA-event durations of the phases, recorded on the stream
+ *                mot_march ran on, only while profiling is enabled:
+ *                forward FFT of J_{n-1}, lag MAC, inverse FFT, rhs + CG solve       */
+typedef struct {
+    long long launches;
+    long long mac_launches;
+    long long steps;
+    long long cg_iters;
+    double ms_fft_fwd;
+    double ms_mac;
+    double ms_fft_inv;
+    double ms_solve;
+} mot_stats;
+
+/* Enable (1) or disable (0) per-phase event timing in mot_march and reset the
+ * counters.  Timing adds five event records per step. */
+mot_status mot_set_profiling(mot_ctx* ctx, int enable);
+
+/* Copy the counters (see mot_stats) to *out (host pointer). */
+mot_status mot_get_stats(const mot_ctx* ctx, mot_stats* out);
+
+/* Last error message of ctx, or of the last failed mot_create when ctx is NULL. */
+const char* mot_last_error(const mot_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MOT_H */

@@ -1,0 +1,455 @@
+// C ABI of the marching library: context lifetime, excitation staging and the step
+// loop (Eqs. MOTInversion, PnMOT).  Per step n:
+//   1. forward FFT of J_{n-1} into the spectral ring        (Sec. 3)
+//   2. lag MAC over the ring, inverse FFT -> (G * J)_hist    (Eq. PnFFTMOT)
+//   3. FIR epilogue -> rhs, CG solve of Z_0 J_n = rhs        (Eq. MOTInversion, Sec. 6.1)
+//   4. ||J_n|| monitor, optional AoS write-out
+#include "mot_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace {
+
+thread_local std::string g_create_error;
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool smooth7(int n) {
+    for (int r : {2, 3, 5, 7})
+        while (n % r == 0) n /= r;
+    return n == 1;
+}
+
+int pad_size(int N) {
+    int P = std::max(2 * N - 1, 2);
+    while (P % 2 != 0 || !smooth7(P)) ++P;
+    return P;
+}
+
+template <typename F>
+mot_status guarded(mot_ctx* c, F&& f) {
+    if (c && c->broken) return MOT_ERR_STATE;
+    try {
+        f();
+        return MOT_OK;
+    } catch (const MotError& e) {
+        if (c) {
+            c->err = e.msg;
+            if (e.st == MOT_ERR_CUDA || e.st == MOT_ERR_TIMEOUT) c->broken = true;
+        }
+        return e.st;
+    } catch (const std::bad_alloc&) {
+        if (c) c->err = "host allocation failed";
+        return MOT_ERR_OOM;
+    }
+}
+
+template <typename R> void alloc_history(mot_ctx* c) { mot::history_alloc<R>(c); }
+
+void free_all(mot_ctx* c) {
+    for (int a = 0; a < 3; ++a) mot::fft_free_axis(c->ax[a]);
+    mot::history_free<double>(c);
+    mot::history_free<float>(c);
+    double* dptrs[] = {c->eps, c->chi, c->cg_diag, c->J, c->rhs, c->cg_r, c->cg_p,
+                       c->cg_q, c->red, c->norms, c->outbuf, c->tab, c->Estage};
+    for (double* p : dptrs) cudaFree(p);
+    cudaFree(c->tab_l0);
+    cudaFree(c->dstatus);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    c->events.clear();
+    if (c->stream) cudaStreamDestroy(c->stream);
+}
+
+void reset_state(mot_ctx* c, cudaStream_t s) {
+    MOT_CUDA_TRY(cudaMemsetAsync(c->J, 0, sizeof(double) * 3 * c->M * c->jring, s));
+    if (c->precision == MOT_FP64) mot::history_reset<double>(c, s);
+    else mot::history_reset<float>(c, s);
+    c->n_done = 0;
+    c->E_count = 0;
+    c->peak_norm = 0.0;
+    c->last_norm = 0.0;
+    c->fail_step = 0;
+}
+
+void history_for(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t e1 = nullptr,
+                 cudaEvent_t e2 = nullptr) {
+    if (c->precision == MOT_FP64) mot::history_step<double>(c, n, s, e1, e2);
+    else mot::history_step<float>(c, n, s, e1, e2);
+}
+
+void ensure_events(mot_ctx* c, size_t n) {
+    while (c->events.size() < n) {
+        cudaEvent_t e;
+        MOT_CUDA_TRY(cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+mot_status mot_create(const int grid[3], const double h[3], double dt, const double* eps_r,
+                      const double* fir_taps, int n_taps, int precision, int scheme, int block,
+                      mot_ctx** out) {
+    if (out) *out = nullptr;
+    g_create_error.clear();
+    auto fail = [](mot_status st, const std::string& m) {
+        g_create_error = m;
+        return st;
+    };
+    if (!grid || !h || !eps_r || !out) return fail(MOT_ERR_ARG, "null argument");
+    for (int a = 0; a < 3; ++a)
+        if (grid[a] < 1 || grid[a] > 4096) return fail(MOT_ERR_ARG, "grid sizes must be in 1..4096");
+    if (!(h[0] > 0) || h[0] != h[1] || h[0] != h[2])
+        return fail(MOT_ERR_ARG, "voxels must be cubes (h[0] == h[1] == h[2] > 0)");
+    if (!(dt > 0) || std::fabs(dt - h[0]) > 1e-12 * h[0])
+        return fail(MOT_ERR_ARG, "the element quadrature requires c0 dt == h (c0 = 1)");
+    if (n_taps < 0 || n_taps > 64 || (n_taps > 0 && !fir_taps))
+        return fail(MOT_ERR_ARG, "n_taps must be 0..64 and fir_taps non-null when n_taps > 0");
+    if (precision != MOT_FP64 && precision != MOT_FP32_HISTORY)
+        return fail(MOT_ERR_ARG, "unknown precision");
+    if (scheme != MOT_HISTORY_DIRECT)
+        return fail(MOT_ERR_ARG, "unknown history scheme");
+    const long long M = (long long)grid[0] * grid[1] * grid[2];
+    for (long long m = 0; m < M; ++m)
+        if (!(eps_r[m] >= 1.0) || !std::isfinite(eps_r[m]))
+            return fail(MOT_ERR_ARG, "eps_r must be finite and >= 1");
+
+    mot_ctx* c = new (std::nothrow) mot_ctx();
+    if (!c) return fail(MOT_ERR_OOM, "host allocation failed");
+    c->U = grid[0]; c->V = grid[1]; c->W = grid[2];
+    c->M = M;
+    c->precision = precision;
+    c->scheme = scheme;
+    c->block = block;
+    c->n_taps = n_taps;
+    c->taps.assign(fir_taps, fir_taps + n_taps);
+    // Eq. Ell with h = c dt = 1
+    c->ell = (int)std::floor(std::sqrt((double)c->U * c->U + (double)c->V * c->V +
+                                       (double)c->W * c->W)) + 2;
+    mot_status st = guarded(c, [&] {
+        int dev = 0;
+        MOT_CUDA_TRY(cudaGetDevice(&dev));
+        MOT_CUDA_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+        MOT_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        const int N[3] = {c->U, c->V, c->W};
+        for (int a = 0; a < 3; ++a) mot::fft_plan_axis(c->ax[a], pad_size(N[a]));
+        c->Hu = c->ax[0].P / 2 + 1;
+        c->Hv = c->ax[1].P / 2 + 1;
+        c->Hw = c->ax[2].P / 2 + 1;
+        c->nbins = (long long)c->ax[2].P * c->ax[1].P * c->Hu;
+        c->noct = (long long)c->Hw * c->Hv * c->Hu;
+        // geometry
+        std::vector<double> e(eps_r, eps_r + M), chi(M), dg(M);
+        const double d0 = n_taps > 0 ? fir_taps[0] : 0.0;
+        for (long long m = 0; m < M; ++m) {
+            chi[m] = (e[m] - 1.0) / e[m];
+            dg[m] = chi[m] > 0.0 ? (0.5 / e[m] + d0) / chi[m] : 0.0;
+        }
+        MOT_CUDA_TRY(cudaMalloc(&c->eps, sizeof(double) * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->chi, sizeof(double) * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg_diag, sizeof(double) * M));
+        MOT_CUDA_TRY(cudaMemcpy(c->eps, e.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+        MOT_CUDA_TRY(cudaMemcpy(c->chi, chi.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+        MOT_CUDA_TRY(cudaMemcpy(c->cg_diag, dg.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+        // elements, stencil, spectra
+        mot::compute_table(c);
+        mot::stencil_setup(c);
+        if (precision == MOT_FP64) alloc_history<double>(c);
+        else alloc_history<float>(c);
+        mot::compute_spectra(c);
+        // marching state
+        c->jring = std::max(n_taps, 4) + 1;
+        MOT_CUDA_TRY(cudaMalloc(&c->J, sizeof(double) * 3 * M * c->jring));
+        MOT_CUDA_TRY(cudaMalloc(&c->rhs, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg_r, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg_p, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg_q, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
+        MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
+        MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
+        reset_state(c, c->stream);
+        MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+    if (st != MOT_OK) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return MOT_OK;
+}
+
+void mot_destroy(mot_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+mot_status mot_set_excitation(mot_ctx* c, int n_steps, const double* E, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_steps < 1 || !E) { c->err = "n_steps >= 1 and E non-null required"; return MOT_ERR_ARG; }
+    return guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        if (n_steps > c->E_cap) {
+            MOT_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(c->Estage);
+            c->Estage = nullptr;
+            c->E_cap = 0;
+            MOT_CUDA_TRY(cudaMalloc(&c->Estage, sizeof(double) * 3 * c->M * n_steps));
+            c->E_cap = n_steps;
+        }
+        MOT_CUDA_TRY(cudaMemcpyAsync(c->Estage, E, sizeof(double) * 3 * c->M * n_steps,
+                                     is_device_ptr(E) ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, s));
+        c->E_first = c->n_done + 1;
+        c->E_count = n_steps;
+    });
+}
+
+mot_status mot_plane_wave(mot_ctx* c, const double k_hat[3], const double p_hat[3], double f_c,
+                          double sigma_t, double t0, int n_first, int n_steps, double* E_out,
+                          void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (!k_hat || !p_hat || !E_out || n_steps < 1 || !(sigma_t > 0)) {
+        c->err = "invalid plane-wave arguments";
+        return MOT_ERR_ARG;
+    }
+    return guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        if (is_device_ptr(E_out)) {
+            mot::plane_wave(c, k_hat, p_hat, f_c, sigma_t, t0, n_first, n_steps, E_out, s);
+        } else {
+            double* tmp = nullptr;
+            MOT_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * 3 * c->M * n_steps));
+            try {
+                mot::plane_wave(c, k_hat, p_hat, f_c, sigma_t, t0, n_first, n_steps, tmp, s);
+                MOT_CUDA_TRY(cudaMemcpyAsync(E_out, tmp, sizeof(double) * 3 * c->M * n_steps,
+                                             cudaMemcpyDeviceToHost, s));
+                MOT_CUDA_TRY(cudaStreamSynchronize(s));
+            } catch (...) {
+                cudaFree(tmp);
+                throw;
+            }
+            cudaFree(tmp);
+        }
+    });
+}
+
+mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_steps < 1) { c->err = "n_steps must be >= 1"; return MOT_ERR_ARG; }
+    mot_status result = MOT_OK;
+    mot_status st = guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        const bool dev_out = is_device_ptr(J_out);
+        if (n_steps > c->norms_cap) {
+            MOT_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(c->norms);
+            c->norms = nullptr;
+            c->norms_cap = 0;
+            MOT_CUDA_TRY(cudaMalloc(&c->norms, sizeof(double) * n_steps));
+            c->norms_cap = n_steps;
+        }
+        if (J_out && !dev_out && !c->outbuf)
+            MOT_CUDA_TRY(cudaMalloc(&c->outbuf, sizeof(double) * 3 * c->M));
+        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
+        if (c->profiling) ensure_events(c, 5 * (size_t)n_steps);
+        for (int i = 0; i < n_steps; ++i) {
+            const int n = c->n_done + 1 + i;
+            const double* En = nullptr;
+            if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count)
+                En = c->Estage + (long long)(n - c->E_first) * 3 * c->M;
+            cudaEvent_t* ev = c->profiling ? &c->events[5 * (size_t)i] : nullptr;
+            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
+            history_for(c, n, s, ev ? ev[1] : nullptr, ev ? ev[2] : nullptr);
+            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[3], s));
+            mot::solve_step(c, n, En, c->norms + i, s);
+            c->stats.launches += 2;
+            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[4], s));
+            if (J_out) {
+                double* dst = J_out + (long long)i * 3 * c->M;
+                if (dev_out) {
+                    mot::write_aos(c, n, dst, s);
+                } else {
+                    mot::write_aos(c, n, c->outbuf, s);
+                    MOT_CUDA_TRY(cudaMemcpyAsync(dst, c->outbuf, sizeof(double) * 3 * c->M,
+                                                 cudaMemcpyDeviceToHost, s));
+                }
+                c->stats.launches += 1;
+            }
+        }
+        std::vector<double> nrm(n_steps);
+        int hs[4];
+        MOT_CUDA_TRY(cudaMemcpyAsync(nrm.data(), c->norms, sizeof(double) * n_steps,
+                                     cudaMemcpyDeviceToHost, s));
+        MOT_CUDA_TRY(cudaMemcpyAsync(hs, c->dstatus, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+        const int n0 = c->n_done;
+        c->n_done += n_steps;
+        c->last_iters = hs[0];
+        c->stats.steps += n_steps;
+        c->stats.cg_iters += hs[3];
+        if (c->profiling) {
+            for (int i = 0; i < n_steps; ++i) {
+                float t[4];
+                cudaEvent_t* ev = &c->events[5 * (size_t)i];
+                for (int k = 0; k < 4; ++k) MOT_CUDA_TRY(cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
+                c->stats.ms_fft_fwd += t[0];
+                c->stats.ms_mac += t[1];
+                c->stats.ms_fft_inv += t[2];
+                c->stats.ms_solve += t[3];
+            }
+        }
+        for (int i = 0; i < n_steps; ++i) {
+            const double v = std::sqrt(nrm[i]);
+            const bool bad = !std::isfinite(v) ||
+                             (c->peak_norm > 0.0 && v > c->growth * c->peak_norm);
+            if (bad && result == MOT_OK) {
+                result = MOT_ERR_UNSTABLE;
+                if (!c->fail_step) c->fail_step = n0 + 1 + i;
+                char b[160];
+                snprintf(b, sizeof b, "unstable: ||J_%d|| = %g (peak so far %g)", n0 + 1 + i, v,
+                         c->peak_norm);
+                c->err = b;
+            }
+            if (std::isfinite(v)) c->peak_norm = std::max(c->peak_norm, v);
+            c->last_norm = v;
+        }
+        if (result == MOT_OK && (hs[1] & 1)) {
+            result = MOT_ERR_NOT_CONVERGED;
+            if (!c->fail_step) c->fail_step = hs[2];
+            char b[160];
+            snprintf(b, sizeof b, "CG did not converge within %d iterations at step %d",
+                     c->max_iter, hs[2]);
+            c->err = b;
+        }
+    });
+    return st != MOT_OK ? st : result;
+}
+
+mot_status mot_eval_history(mot_ctx* c, int n_hist, const double* J_hist, double* P_out,
+                            void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_hist < 1 || n_hist > c->ell || !J_hist || !P_out) {
+        c->err = "n_hist must be in 1..ell and buffers non-null";
+        return MOT_ERR_ARG;
+    }
+    return guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        reset_state(c, s);
+        const long long step = 3 * c->M;
+        double* tmp = nullptr;
+        MOT_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * step * (n_hist + 1)));
+        try {
+            MOT_CUDA_TRY(cudaMemcpyAsync(tmp, J_hist, sizeof(double) * step * n_hist,
+                                         is_device_ptr(J_hist) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice, s));
+            const int n = n_hist + 1;
+            // J_{n-k} = J_hist[k-1]; march the rings forward through times 1..n_hist
+            for (int t = 1; t <= n_hist; ++t) {
+                mot::read_aos(c, tmp + (long long)(n - 1 - t) * step,
+                              c->J + mot::slot_index(t, c->jring) * step, s);
+                if (t < n_hist) history_for(c, t + 1, s);   // FFT of J_t into the ring
+            }
+            history_for(c, n, s);
+            mot::history_out(c, n, tmp + (long long)n_hist * step, s);
+            MOT_CUDA_TRY(cudaMemcpyAsync(P_out, tmp + (long long)n_hist * step, sizeof(double) * step,
+                                         is_device_ptr(P_out) ? cudaMemcpyDeviceToDevice
+                                                              : cudaMemcpyDeviceToHost, s));
+            MOT_CUDA_TRY(cudaStreamSynchronize(s));
+        } catch (...) {
+            cudaFree(tmp);
+            throw;
+        }
+        cudaFree(tmp);
+        reset_state(c, s);
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+}
+
+mot_status mot_get_table(mot_ctx* c, int l0, int n_lags, double* out) {
+    if (!c) return MOT_ERR_ARG;
+    if (l0 < 0 || n_lags < 1 || l0 + n_lags > c->ell + 1 || !out) {
+        c->err = "lag range must lie in 0..ell";
+        return MOT_ERR_ARG;
+    }
+    return guarded(c, [&] {
+        const long long noff = (long long)c->U * c->V * c->W;
+        std::vector<int> L0(noff);
+        std::vector<double> tab(noff * 6 * mot::WIN);
+        MOT_CUDA_TRY(cudaMemcpy(L0.data(), c->tab_l0, sizeof(int) * noff, cudaMemcpyDeviceToHost));
+        MOT_CUDA_TRY(cudaMemcpy(tab.data(), c->tab, sizeof(double) * tab.size(),
+                                cudaMemcpyDeviceToHost));
+        for (int li = 0; li < n_lags; ++li)
+            for (int cc = 0; cc < 6; ++cc)
+                for (long long o = 0; o < noff; ++o) {
+                    const int idx = l0 + li - L0[o];
+                    out[((long long)li * 6 + cc) * noff + o] =
+                        (idx >= 0 && idx < mot::WIN) ? tab[(o * 6 + cc) * mot::WIN + idx] : 0.0;
+                }
+    });
+}
+
+mot_status mot_get_spectrum(mot_ctx* c, int l, double* out) {
+    if (!c) return MOT_ERR_ARG;
+    if (l < 1 || l > c->ell || !out) { c->err = "lag must be in 1..ell"; return MOT_ERR_ARG; }
+    return guarded(c, [&] { mot::spectrum_of_lag(c, l, out); });
+}
+
+mot_status mot_get_info(const mot_ctx* c, int* ell, int P[3], int* n_done, double* last_norm,
+                        int* fail_step, int* last_cg_iters) {
+    if (!c) return MOT_ERR_ARG;
+    if (ell) *ell = c->ell;
+    if (P) for (int a = 0; a < 3; ++a) P[a] = c->ax[a].P;
+    if (n_done) *n_done = c->n_done;
+    if (last_norm) *last_norm = c->last_norm;
+    if (fail_step) *fail_step = c->fail_step;
+    if (last_cg_iters) *last_cg_iters = c->last_iters;
+    return c->broken ? MOT_ERR_STATE : MOT_OK;
+}
+
+mot_status mot_set_solver(mot_ctx* c, double tol, int max_iter, double growth_limit) {
+    if (!c) return MOT_ERR_ARG;
+    if (!(tol > 0) || max_iter < 1 || !(growth_limit > 1)) {
+        c->err = "tol > 0, max_iter >= 1 and growth_limit > 1 required";
+        return MOT_ERR_ARG;
+    }
+    c->tol = tol;
+    c->max_iter = max_iter;
+    c->growth = growth_limit;
+    return MOT_OK;
+}
+
+mot_status mot_set_profiling(mot_ctx* c, int enable) {
+    if (!c) return MOT_ERR_ARG;
+    c->profiling = enable != 0;
+    c->stats = mot_stats{};
+    return MOT_OK;
+}
+
+mot_status mot_get_stats(const mot_ctx* c, mot_stats* out) {
+    if (!c || !out) return MOT_ERR_ARG;
+    *out = c->stats;
+    return MOT_OK;
+}
+
+const char* mot_last_error(const mot_ctx* c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

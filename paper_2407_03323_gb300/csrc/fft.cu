@@ -1,0 +1,456 @@
+// Zero-padded 3D FFTs of the current densities and of the history spectrum
+// (Sec. 3, Eq. PnFFTMOT; App. A: a Toeplitz product becomes a circulant one after
+// zero-padding to P >= n_row + n_col - 1 per axis).
+//
+// Layouts (per component, 3 components stacked):
+//   spatial   [W][V][U]        u fastest (m = u + U (v + V w), Sec. 2.2)
+//   after x   [W][V][Hu]       Hu = Pu/2 + 1 (real-to-complex along u)
+//   after y   [W][Pv][Hu]
+//   spectrum  [Pw][Pv][Hu]
+// Forward: three passes x (r2c of paired real rows), y, z; every pass reads only the
+// nonzero (unpadded) inputs.  Inverse: z, y, x (c2r), storing only the N outputs the
+// grid needs.  Each pass runs batched length-P transforms in shared memory: a CTA
+// holds a tile of TB lines as buf[j * (TB+1) + t] and runs mixed-radix Stockham
+// stages (radices 2, 3, 4, 5, 7) over it.  Twiddles come from a table of
+// exp(-2 pi i k / P) built once per axis with sincospi.  No normalisation is applied.
+#include "mot_internal.cuh"
+
+#include <algorithm>
+
+namespace {
+
+constexpr int NT = 256;
+
+template <typename R> struct Tile { static constexpr int TB = 16; };
+template <> struct Tile<float> { static constexpr int TB = 32; };
+
+// ------------------------------------------------------------------ butterflies
+// dir = -1 forward (exp(-i...)), +1 inverse; W(m) = exp(dir 2 pi i m / P) from table
+template <typename C>
+__device__ __forceinline__ C twid(const C* tw, int m, int dir) {
+    C w = tw[m];
+    if (dir > 0) w.y = -w.y;
+    return w;
+}
+
+template <typename C, int R>
+__device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
+    if constexpr (R == 2) {
+        C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        C b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+        // -i * dir' : forward multiplies b1 by -i, inverse by +i
+        C jb1;
+        if (dir < 0) { jb1.x = b1.y; jb1.y = -b1.x; } else { jb1.x = -b1.y; jb1.y = b1.x; }
+        v[0] = cadd(a0, b0);
+        v[2] = csub(a0, b0);
+        v[1] = cadd(a1, jb1);
+        v[3] = csub(a1, jb1);
+    } else {
+        // odd radix: out[q] = v0 + sum_r (s_r cos(2 pi q r/R) -/+ i d_r sin(2 pi q r/R))
+        constexpr int H = (R - 1) / 2;
+        C s[H], d[H];
+        C v0 = v[0];
+        C sum = v0;
+#pragma unroll
+        for (int r = 1; r <= H; ++r) {
+            s[r - 1] = cadd(v[r], v[R - r]);
+            d[r - 1] = csub(v[r], v[R - r]);
+            sum = cadd(sum, s[r - 1]);
+        }
+        const int step = P / R;
+#pragma unroll
+        for (int q = 1; q <= H; ++q) {
+            C A = v0, B;
+            B.x = 0; B.y = 0;
+#pragma unroll
+            for (int r = 1; r <= H; ++r) {
+                const C w = tw[((q * r) % R) * step];   // cos - i sin (forward table)
+                const auto cs = w.x, sn = -w.y;
+                A.x += s[r - 1].x * cs;
+                A.y += s[r - 1].y * cs;
+                B.x += d[r - 1].x * sn;
+                B.y += d[r - 1].y * sn;
+            }
+            // forward: out[q] = A - i B, out[R-q] = A + i B ; inverse: swapped
+            C mB;   // -i B
+            mB.x = B.y; mB.y = -B.x;
+            if (dir < 0) {
+                v[q] = cadd(A, mB);
+                v[R - q] = csub(A, mB);
+            } else {
+                v[q] = csub(A, mB);
+                v[R - q] = cadd(A, mB);
+            }
+        }
+        v[0] = sum;
+    }
+}
+
+template <typename C, int R>
+__device__ __forceinline__ void stage(const C* __restrict__ x, C* __restrict__ y, int P, int Ns,
+                                      int TB, int ld, const C* tw, int dir) {
+    const int nb = P / R;
+    const int items = nb * TB;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int t = it % TB, j = it / TB;
+        const int k = j % Ns;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = x[(j + r * nb) * ld + t];
+        if (Ns > 1) {
+            const int tstep = P / (Ns * R);
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid(tw, (r * k * tstep) % P, dir));
+        }
+        dft_small<C, R>(v, tw, P, dir);
+        const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) y[(base + r * Ns) * ld + t] = v[r];
+    }
+}
+
+// runs all stages; returns the buffer holding the result
+template <typename C>
+__device__ C* fft_tile(C* b0, C* b1, int P, const int* rad, int nrad, int TB, int ld,
+                       const C* tw, int dir) {
+    int Ns = 1;
+    C* x = b0;
+    C* y = b1;
+    for (int s = 0; s < nrad; ++s) {
+        const int R = rad[s];
+        switch (R) {
+            case 2: stage<C, 2>(x, y, P, Ns, TB, ld, tw, dir); break;
+            case 3: stage<C, 3>(x, y, P, Ns, TB, ld, tw, dir); break;
+            case 4: stage<C, 4>(x, y, P, Ns, TB, ld, tw, dir); break;
+            case 5: stage<C, 5>(x, y, P, Ns, TB, ld, tw, dir); break;
+            case 7: stage<C, 7>(x, y, P, Ns, TB, ld, tw, dir); break;
+        }
+        __syncthreads();
+        Ns *= R;
+        C* tmp = x; x = y; y = tmp;
+    }
+    return x;
+}
+
+struct RadixList {
+    int P;
+    int n;
+    int r[16];
+};
+
+template <typename C>
+__device__ __forceinline__ void load_tw(C* stw, const C* tw, int P) {
+    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+}
+
+// ------------------------------------------------------------------ pass x, forward
+// rows (comp, w, v) of a real [3][W][V][U] array, paired (v, v+1) -> [3][W][V][Hu]
+template <typename R>
+__global__ void __launch_bounds__(NT) k_fwd_x(const double* __restrict__ in, int U, int V, int W,
+                                              typename CT<R>::c* __restrict__ out,
+                                              const typename CT<R>::c* __restrict__ tw,
+                                              RadixList rl) {
+    typedef typename CT<R>::c C;
+    constexpr int TB = Tile<R>::TB;
+    constexpr int ld = TB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stw = reinterpret_cast<C*>(smem_raw);
+    C* b0 = stw + rl.P;
+    C* b1 = b0 + rl.P * ld;
+    const int P = rl.P, Hu = P / 2 + 1;
+    const int VP = (V + 1) / 2;
+    const long long npairs = 3LL * W * VP;
+    const long long pair0 = (long long)blockIdx.x * TB;
+    load_tw(stw, tw, P);
+    // load: z = a + i b, zero-padded
+    for (int it = threadIdx.x; it < TB * P; it += blockDim.x) {
+        const int t = it / P, j = it % P;
+        const long long pr = pair0 + t;
+        C z;
+        z.x = 0; z.y = 0;
+        if (pr < npairs && j < U) {
+            const long long cw = pr / VP;
+            const int v = (int)(pr % VP) * 2;
+            const double* row = in + (cw * V + v) * (long long)U;
+            z.x = (R)row[j];
+            if (v + 1 < V) z.y = (R)row[U + j];
+        }
+        b0[j * ld + t] = z;
+    }
+    __syncthreads();
+    C* res = fft_tile(b0, b1, P, rl.r, rl.n, TB, ld, stw, -1);
+    // split: A = (Z[k] + conj Z[P-k]) / 2, B = -i (Z[k] - conj Z[P-k]) / 2
+    for (int it = threadIdx.x; it < TB * Hu; it += blockDim.x) {
+        const int t = it / Hu, k = it % Hu;
+        const long long pr = pair0 + t;
+        if (pr >= npairs) continue;
+        const long long cw = pr / VP;
+        const int v = (int)(pr % VP) * 2;
+        const C zk = res[k * ld + t];
+        const C zm = res[((P - k) % P) * ld + t];
+        C A, B;
+        A.x = (R)0.5 * (zk.x + zm.x);
+        A.y = (R)0.5 * (zk.y - zm.y);
+        B.x = (R)0.5 * (zk.y + zm.y);
+        B.y = (R)0.5 * (zm.x - zk.x);
+        out[(cw * V + v) * (long long)Hu + k] = A;
+        if (v + 1 < V) out[(cw * V + v + 1) * (long long)Hu + k] = B;
+    }
+}
+
+// ------------------------------------------------------------------ pass x, inverse
+// [3][W][V][Hu] Hermitian halves -> real rows [3][W][V][U] (first U outputs)
+template <typename R>
+__global__ void __launch_bounds__(NT) k_inv_x(const typename CT<R>::c* __restrict__ in, int U,
+                                              int V, int W, R* __restrict__ out,
+                                              const typename CT<R>::c* __restrict__ tw,
+                                              RadixList rl) {
+    typedef typename CT<R>::c C;
+    constexpr int TB = Tile<R>::TB;
+    constexpr int ld = TB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stw = reinterpret_cast<C*>(smem_raw);
+    C* b0 = stw + rl.P;
+    C* b1 = b0 + rl.P * ld;
+    const int P = rl.P, Hu = P / 2 + 1;
+    const int VP = (V + 1) / 2;
+    const long long npairs = 3LL * W * VP;
+    const long long pair0 = (long long)blockIdx.x * TB;
+    load_tw(stw, tw, P);
+    for (int it = threadIdx.x; it < TB * Hu; it += blockDim.x) {
+        const int t = it / Hu, k = it % Hu;
+        const long long pr = pair0 + t;
+        C A, B;
+        A.x = 0; A.y = 0; B.x = 0; B.y = 0;
+        if (pr < npairs) {
+            const long long cw = pr / VP;
+            const int v = (int)(pr % VP) * 2;
+            A = in[(cw * V + v) * (long long)Hu + k];
+            if (v + 1 < V) B = in[(cw * V + v + 1) * (long long)Hu + k];
+        }
+        C z;
+        z.x = A.x - B.y;
+        z.y = A.y + B.x;
+        b0[k * ld + t] = z;
+        if (k >= 1 && k < P - k) {
+            C zm;
+            zm.x = A.x + B.y;
+            zm.y = B.x - A.y;
+            b0[(P - k) * ld + t] = zm;
+        }
+    }
+    __syncthreads();
+    C* res = fft_tile(b0, b1, P, rl.r, rl.n, TB, ld, stw, +1);
+    for (int it = threadIdx.x; it < TB * U; it += blockDim.x) {
+        const int t = it / U, j = it % U;
+        const long long pr = pair0 + t;
+        if (pr >= npairs) continue;
+        const long long cw = pr / VP;
+        const int v = (int)(pr % VP) * 2;
+        const C z = res[j * ld + t];
+        out[(cw * V + v) * (long long)U + j] = z.x;
+        if (v + 1 < V) out[(cw * V + v + 1) * (long long)U + j] = z.y;
+    }
+}
+
+// ------------------------------------------------------------------ strided passes
+struct MidArgs {
+    int n_in, n_out;          // inputs read / outputs stored along the axis
+    int n_o2;                 // outer index o = comp * n_o2 + o2
+    long long in_c, in_o, in_a;    // strides: component, outer, axis (in elements)
+    long long out_c, out_o, out_a;
+    int Hu;                   // contiguous extent tiled by TB
+    int dir;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(NT) k_mid(const typename CT<R>::c* __restrict__ in,
+                                            typename CT<R>::c* __restrict__ out,
+                                            const typename CT<R>::c* __restrict__ tw,
+                                            RadixList rl, MidArgs a) {
+    typedef typename CT<R>::c C;
+    constexpr int TB = Tile<R>::TB;
+    constexpr int ld = TB + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stw = reinterpret_cast<C*>(smem_raw);
+    C* b0 = stw + rl.P;
+    C* b1 = b0 + rl.P * ld;
+    const int P = rl.P;
+    const int ntile = (a.Hu + TB - 1) / TB;
+    const long long o = blockIdx.x / ntile;
+    const int ku0 = (int)(blockIdx.x % ntile) * TB;
+    const long long comp = o / a.n_o2, o2 = o % a.n_o2;
+    const C* src = in + comp * a.in_c + o2 * a.in_o + ku0;
+    C* dst = out + comp * a.out_c + o2 * a.out_o + ku0;
+    load_tw(stw, tw, P);
+    for (int it = threadIdx.x; it < P * TB; it += blockDim.x) {
+        const int j = it / TB, t = it % TB;
+        C z;
+        z.x = 0; z.y = 0;
+        if (j < a.n_in && ku0 + t < a.Hu) z = src[j * a.in_a + t];
+        b0[j * ld + t] = z;
+    }
+    __syncthreads();
+    C* res = fft_tile(b0, b1, P, rl.r, rl.n, TB, ld, stw, a.dir);
+    for (int it = threadIdx.x; it < a.n_out * TB; it += blockDim.x) {
+        const int j = it / TB, t = it % TB;
+        if (ku0 + t < a.Hu) dst[j * a.out_a + t] = res[j * ld + t];
+    }
+}
+
+RadixList radix_list(const AxisFFT& ax) {
+    RadixList rl;
+    rl.P = ax.P;
+    rl.n = ax.nrad;
+    for (int i = 0; i < 16; ++i) rl.r[i] = ax.rad[i];
+    return rl;
+}
+
+template <typename R> const typename CT<R>::c* table(const AxisFFT& a);
+template <> const double2* table<double>(const AxisFFT& a) { return a.tw64; }
+template <> const float2* table<float>(const AxisFFT& a) { return a.tw32; }
+
+template <typename R> size_t smem_bytes(int P) {
+    typedef typename CT<R>::c C;
+    return sizeof(C) * ((size_t)P + 2 * (size_t)P * (Tile<R>::TB + 1));
+}
+
+template <typename K> void set_smem(K kern, size_t bytes) {
+    MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+__global__ void twiddle_kernel(int P, double2* t64, float2* t32) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= P) return;
+    double s, c;
+    sincospi(2.0 * (double)k / (double)P, &s, &c);
+    t64[k] = make_double2(c, -s);
+    t32[k] = make_float2((float)c, (float)-s);
+}
+
+}  // namespace
+
+namespace mot {
+
+void fft_plan_axis(AxisFFT& a, int P) {
+    a.P = P;
+    a.nrad = 0;
+    int n = P;
+    while (n % 4 == 0) { a.rad[a.nrad++] = 4; n /= 4; }
+    while (n % 2 == 0) { a.rad[a.nrad++] = 2; n /= 2; }
+    for (int r : {3, 5, 7})
+        while (n % r == 0) { a.rad[a.nrad++] = r; n /= r; }
+    if (n != 1) throw MotError{MOT_ERR_ARG, "FFT length has a prime factor above 7"};
+    MOT_CUDA_TRY(cudaMalloc(&a.tw64, sizeof(double2) * P));
+    MOT_CUDA_TRY(cudaMalloc(&a.tw32, sizeof(float2) * P));
+    twiddle_kernel<<<(P + 255) / 256, 256>>>(P, a.tw64, a.tw32);
+    MOT_LAUNCH_CHECK();
+    MOT_CUDA_TRY(cudaDeviceSynchronize());
+}
+
+void fft_free_axis(AxisFFT& a) {
+    cudaFree(a.tw64);
+    cudaFree(a.tw32);
+    a.tw64 = nullptr;
+    a.tw32 = nullptr;
+}
+
+template <typename R>
+void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s) {
+    typedef typename CT<R>::c C;
+    HistoryBuffers<R>& hb = hbuf<R>(c);
+    constexpr int TB = Tile<R>::TB;
+    const int U = c->U, V = c->V, W = c->W;
+    const int Pu = c->ax[0].P, Pv = c->ax[1].P, Pw = c->ax[2].P, Hu = c->Hu;
+    // x
+    {
+        const long long npairs = 3LL * W * ((V + 1) / 2);
+        const size_t sm = smem_bytes<R>(Pu);
+        set_smem(k_fwd_x<R>, sm);
+        k_fwd_x<R><<<(int)((npairs + TB - 1) / TB), NT, sm, s>>>(Jsoa, U, V, W, hb.tmp1,
+                                                                 table<R>(c->ax[0]),
+                                                                 radix_list(c->ax[0]));
+        MOT_LAUNCH_CHECK();
+    }
+    const int ntile = (Hu + TB - 1) / TB;
+    // y: [3][W][V][Hu] -> [3][W][Pv][Hu]
+    {
+        MidArgs a;
+        a.n_in = V; a.n_out = Pv; a.n_o2 = W;
+        a.in_c = (long long)W * V * Hu; a.in_o = (long long)V * Hu; a.in_a = Hu;
+        a.out_c = (long long)W * Pv * Hu; a.out_o = (long long)Pv * Hu; a.out_a = Hu;
+        a.Hu = Hu; a.dir = -1;
+        const size_t sm = smem_bytes<R>(Pv);
+        set_smem(k_mid<R>, std::max(sm, smem_bytes<R>(Pw)));
+        k_mid<R><<<3 * W * ntile, NT, sm, s>>>(hb.tmp1, hb.tmp2, table<R>(c->ax[1]),
+                                               radix_list(c->ax[1]), a);
+        MOT_LAUNCH_CHECK();
+    }
+    // z: [3][W][Pv][Hu] -> [3][Pw][Pv][Hu]
+    {
+        MidArgs a;
+        a.n_in = W; a.n_out = Pw; a.n_o2 = Pv;
+        a.in_c = (long long)W * Pv * Hu; a.in_o = Hu; a.in_a = (long long)Pv * Hu;
+        a.out_c = (long long)Pw * Pv * Hu; a.out_o = Hu; a.out_a = (long long)Pv * Hu;
+        a.Hu = Hu; a.dir = -1;
+        const size_t sm = smem_bytes<R>(Pw);
+        k_mid<R><<<3 * Pv * ntile, NT, sm, s>>>(hb.tmp2, out, table<R>(c->ax[2]),
+                                                radix_list(c->ax[2]), a);
+        MOT_LAUNCH_CHECK();
+    }
+}
+
+template <typename R>
+void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s) {
+    HistoryBuffers<R>& hb = hbuf<R>(c);
+    constexpr int TB = Tile<R>::TB;
+    const int U = c->U, V = c->V, W = c->W;
+    const int Pu = c->ax[0].P, Pv = c->ax[1].P, Pw = c->ax[2].P, Hu = c->Hu;
+    const int ntile = (Hu + TB - 1) / TB;
+    // z: [3][Pw][Pv][Hu] -> [3][W][Pv][Hu]
+    {
+        MidArgs a;
+        a.n_in = Pw; a.n_out = W; a.n_o2 = Pv;
+        a.in_c = (long long)Pw * Pv * Hu; a.in_o = Hu; a.in_a = (long long)Pv * Hu;
+        a.out_c = (long long)W * Pv * Hu; a.out_o = Hu; a.out_a = (long long)Pv * Hu;
+        a.Hu = Hu; a.dir = +1;
+        const size_t sm = smem_bytes<R>(Pw);
+        set_smem(k_mid<R>, std::max(sm, smem_bytes<R>(Pv)));
+        k_mid<R><<<3 * Pv * ntile, NT, sm, s>>>(in, hb.tmp2, table<R>(c->ax[2]),
+                                                radix_list(c->ax[2]), a);
+        MOT_LAUNCH_CHECK();
+    }
+    // y: [3][W][Pv][Hu] -> [3][W][V][Hu]
+    {
+        MidArgs a;
+        a.n_in = Pv; a.n_out = V; a.n_o2 = W;
+        a.in_c = (long long)W * Pv * Hu; a.in_o = (long long)Pv * Hu; a.in_a = Hu;
+        a.out_c = (long long)W * V * Hu; a.out_o = (long long)V * Hu; a.out_a = Hu;
+        a.Hu = Hu; a.dir = +1;
+        const size_t sm = smem_bytes<R>(Pv);
+        k_mid<R><<<3 * W * ntile, NT, sm, s>>>(hb.tmp2, hb.tmp1, table<R>(c->ax[1]),
+                                               radix_list(c->ax[1]), a);
+        MOT_LAUNCH_CHECK();
+    }
+    // x: c2r
+    {
+        const long long npairs = 3LL * W * ((V + 1) / 2);
+        const size_t sm = smem_bytes<R>(Pu);
+        set_smem(k_inv_x<R>, sm);
+        k_inv_x<R><<<(int)((npairs + TB - 1) / TB), NT, sm, s>>>(hb.tmp1, U, V, W, out,
+                                                                 table<R>(c->ax[0]),
+                                                                 radix_list(c->ax[0]));
+        MOT_LAUNCH_CHECK();
+    }
+}
+
+template void fft_forward<double>(mot_ctx*, const double*, double2*, cudaStream_t);
+template void fft_forward<float>(mot_ctx*, const double*, float2*, cudaStream_t);
+template void fft_inverse<double>(mot_ctx*, const double2*, double*, cudaStream_t);
+template void fft_inverse<float>(mot_ctx*, const float2*, float*, cudaStream_t);
+
+}  // namespace mot

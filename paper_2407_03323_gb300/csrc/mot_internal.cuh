@@ -1,0 +1,176 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "mot.h"
+
+// ------------------------------------------------------------------ complex helpers
+template <typename R> struct CT;
+template <> struct CT<double> { typedef double2 c; };
+template <> struct CT<float>  { typedef float2 c; };
+
+__host__ __device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+__host__ __device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+
+// ------------------------------------------------------------------ status plumbing
+struct MotError {
+    mot_status st;
+    std::string msg;
+};
+
+#define MOT_CUDA_TRY(expr)                                                            \
+    do {                                                                              \
+        cudaError_t e_ = (expr);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            char b_[512];                                                             \
+            snprintf(b_, sizeof b_, "%s failed at %s:%d: %s", #expr, __FILE__,        \
+                     __LINE__, cudaGetErrorString(e_));                               \
+            throw MotError{e_ == cudaErrorMemoryAllocation ? MOT_ERR_OOM : MOT_ERR_CUDA, \
+                           b_};                                                       \
+        }                                                                             \
+    } while (0)
+
+#define MOT_LAUNCH_CHECK() MOT_CUDA_TRY(cudaGetLastError())
+
+// ------------------------------------------------------------------ FFT plan
+// One axis of length P = product of radices (each 2, 3, 4, 5 or 7), Stockham order.
+struct AxisFFT {
+    int P = 0;
+    int nrad = 0;
+    int rad[16] = {0};
+    double2* tw64 = nullptr;  // exp(-2 pi i k / P), k < P (device)
+    float2* tw32 = nullptr;
+};
+
+// Device-side precision-dependent buffers.
+template <typename R> struct HistoryBuffers {
+    typedef typename CT<R>::c C;
+    C* jhat_ring = nullptr;      // [slots][3][Pw][Pv][Hu]
+    R* ghat = nullptr;           // [lags][6][Hw][Hv][Hu] (lag 1 first)
+    C* phat = nullptr;           // [3][Pw][Pv][Hu]
+    C* tmp1 = nullptr;           // FFT intermediates
+    C* tmp2 = nullptr;
+    R* hist_spatial = nullptr;   // [3][W][V][U]   (G * J history, spatial)
+    // blocked temporal scheme
+    C* acc_ring = nullptr;       // [S_max][3][Pw][Pv][Hu] future far-lag sums
+    C* level_spec = nullptr;     // per level kernel temporal spectra (octant)
+};
+
+struct mot_ctx {
+    int U = 0, V = 0, W = 0;
+    long long M = 0;
+    int ell = 0;
+    AxisFFT ax[3];               // x (u), y (v), z (w)
+    int Hu = 0, Hv = 0, Hw = 0;  // P_i / 2 + 1
+    long long nbins = 0;         // Pw * Pv * Hu
+    long long noct = 0;          // Hw * Hv * Hu
+    int precision = 0, scheme = 0, block = 0;
+    int n_taps = 0;
+    std::vector<double> taps;
+    double tol = 1e-13;
+    int max_iter = 200;
+    double growth = 1e12;
+
+    // ring bookkeeping
+    int n_done = 0;              // steps marched
+    int jring = 0;               // spatial J ring slots
+    int hring = 0;               // spectral J ring slots
+
+    // device: geometry and solve
+    double* eps = nullptr;
+    double* chi = nullptr;
+    double* cg_diag = nullptr;   // (T(0)/eps + delta_0)/chi on active voxels, 0 elsewhere
+    double* J = nullptr;         // spatial J ring [jring][3][M] (SoA per slot)
+    double* rhs = nullptr;       // [3][M]
+    double* cg_r = nullptr;
+    double* cg_p = nullptr;
+    double* cg_q = nullptr;
+    double* red = nullptr;       // reduction scratch
+    int* dstatus = nullptr;      // [0] cg iterations of last step, [1] flags
+    double* norms = nullptr;     // per-step ||J_n||^2 of the current call
+    int norms_cap = 0;
+    double* outbuf = nullptr;    // one step of AoS J for host outputs
+    double last_norm = 0.0;
+    double peak_norm = 0.0;
+    int fail_step = 0;
+    int last_iters = 0;
+    double stencil[27 * 6];      // G_0(d) for |d_i| <= 1 (host copy)
+
+    // interaction table (sparse in lag): per octant offset, window of WIN lags
+    int* tab_l0 = nullptr;       // [W*V*U]
+    double* tab = nullptr;       // [W*V*U][6][WIN]
+
+    // excitation staging
+    double* Estage = nullptr;    // [cap][M][3]
+    int E_cap = 0, E_count = 0, E_first = 0;  // steps staged, first staged n
+
+    HistoryBuffers<double> h64;
+    HistoryBuffers<float> h32;
+    int nlev = 0;                // blocked scheme levels
+    int lev_S[8] = {0};
+
+    // counters and optional phase timing
+    mot_stats stats = {};
+    bool profiling = false;
+    std::vector<cudaEvent_t> events;   // 5 per step of the current call
+
+    cudaStream_t stream = nullptr;
+    int nsm = 0;
+    int cg_blocks = 0;
+    bool broken = false;
+    std::string err;
+};
+
+template <typename R> inline HistoryBuffers<R>& hbuf(mot_ctx* c);
+template <> inline HistoryBuffers<double>& hbuf<double>(mot_ctx* c) { return c->h64; }
+template <> inline HistoryBuffers<float>& hbuf<float>(mot_ctx* c) { return c->h32; }
+
+// ------------------------------------------------------------------ internals
+namespace mot {
+
+constexpr int WIN = 8;  // lag window per octant offset of the interaction table
+
+// quadrature.cu
+void compute_table(mot_ctx* c);
+// spectra.cu
+void compute_spectra(mot_ctx* c);
+void spectrum_of_lag(mot_ctx* c, int l, double* host_out);
+// fft.cu
+void fft_plan_axis(AxisFFT& a, int P);
+void fft_free_axis(AxisFFT& a);
+template <typename R>
+void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s);
+template <typename R>
+void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s);
+// history.cu
+template <typename R> void history_alloc(mot_ctx* c);
+template <typename R> void history_free(mot_ctx* c);
+// ev (optional): events recorded after the forward FFT and after the MAC
+template <typename R> void history_step(mot_ctx* c, int n, cudaStream_t s,
+                                        cudaEvent_t ev_fwd = nullptr, cudaEvent_t ev_mac = nullptr);
+template <typename R> void history_reset(mot_ctx* c, cudaStream_t s);
+// solve.cu
+void solve_step(mot_ctx* c, int n, const double* En, double* norm2_out, cudaStream_t s);
+void stencil_setup(mot_ctx* c);
+void write_aos(mot_ctx* c, int n, double* out_dev, cudaStream_t s);
+void read_aos(mot_ctx* c, const double* in_dev, double* slot, cudaStream_t s);
+void history_out(mot_ctx* c, int n, double* out_dev, cudaStream_t s);
+// excitation.cu
+void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, double st,
+                double t0, int n_first, int n_steps, double* Edev, cudaStream_t s);
+
+inline long long slot_index(long long n, long long R) { return ((n % R) + R) % R; }
+
+}  // namespace mot

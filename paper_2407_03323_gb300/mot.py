@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/mot.h (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library libmot.so built in this directory by
+``paper_2407_03323_gb300.build``.  If the library is missing the import of this
+module's entry points raises: there is no CPU path.
+
+Buffers may be numpy arrays (host memory) or torch CUDA tensors (device memory);
+both are passed to the library as raw pointers.  Layouts follow the C ABI:
+eps_r [W][V][U]; excitation and current densities [n][m][b] with
+m = u + U (v + V w) and b = x, y, z.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmot.so")
+
+MOT_OK, MOT_ERR_ARG, MOT_ERR_OOM, MOT_ERR_CUDA = 0, 1, 2, 3
+MOT_ERR_NOT_CONVERGED, MOT_ERR_UNSTABLE, MOT_ERR_TIMEOUT, MOT_ERR_STATE = 4, 5, 6, 7
+STATUS_NAMES = {0: "MOT_OK", 1: "MOT_ERR_ARG", 2: "MOT_ERR_OOM", 3: "MOT_ERR_CUDA",
+                4: "MOT_ERR_NOT_CONVERGED", 5: "MOT_ERR_UNSTABLE", 6: "MOT_ERR_TIMEOUT",
+                7: "MOT_ERR_STATE"}
+PRECISIONS = {"fp64": 0, "fp32_history": 1}
+SCHEMES = {"direct": 0, "blocked": 1}
+
+EXPORTS = ["mot_create", "mot_destroy", "mot_set_excitation", "mot_plane_wave", "mot_march",
+           "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
+           "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_last_error"]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("mac_launches", ctypes.c_longlong),
+                ("steps", ctypes.c_longlong), ("cg_iters", ctypes.c_longlong),
+                ("ms_fft_fwd", ctypes.c_double), ("ms_mac", ctypes.c_double),
+                ("ms_fft_inv", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+
+
+class MotError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libmot.so and declare the signatures; raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libmot.so not found at %s: run `python -m "
+                           "paper_2407_03323_gb300.build` (there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    lib.mot_create.argtypes = [P, P, D, P, P, I, I, I, I, ctypes.POINTER(P)]
+    lib.mot_destroy.argtypes = [P]
+    lib.mot_destroy.restype = None
+    lib.mot_set_excitation.argtypes = [P, I, P, P]
+    lib.mot_plane_wave.argtypes = [P, P, P, D, D, D, I, I, P, P]
+    lib.mot_march.argtypes = [P, I, P, P]
+    lib.mot_eval_history.argtypes = [P, I, P, P, P]
+    lib.mot_get_table.argtypes = [P, I, I, P]
+    lib.mot_get_spectrum.argtypes = [P, I, P]
+    lib.mot_get_info.argtypes = [P, P, P, P, P, P, P]
+    lib.mot_set_solver.argtypes = [P, D, I, D]
+    lib.mot_set_profiling.argtypes = [P, I]
+    lib.mot_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.mot_last_error.argtypes = [P]
+    lib.mot_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("mot_destroy", "mot_last_error"):
+            getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _ptr(buf):
+    """Raw pointer of a numpy array, a torch tensor, or an int; None -> NULL."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be C-contiguous")
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        if hasattr(buf, "is_contiguous") and not buf.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return buf.data_ptr()
+    raise TypeError("unsupported buffer type %r" % type(buf))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_ok(buf):
+    if isinstance(buf, np.ndarray):
+        return buf.dtype == np.float64
+    dt = getattr(buf, "dtype", None)
+    return dt is None or str(dt) == "torch.float64"
+
+
+class Context:
+    """A marching context (mot_create ... mot_destroy)."""
+
+    def __init__(self, eps_r, taps=None, precision="fp64", scheme="direct", block=0, h=1.0):
+        lib = load_library()
+        eps = np.ascontiguousarray(np.asarray(eps_r, dtype=np.float64))
+        if eps.ndim != 3:
+            raise ValueError("eps_r must be [W][V][U]")
+        W, V, U = eps.shape
+        self.shape = (W, V, U)
+        self.M = U * V * W
+        grid = (ctypes.c_int * 3)(U, V, W)
+        hh = (ctypes.c_double * 3)(h, h, h)
+        t = np.ascontiguousarray(np.zeros(0) if taps is None else np.asarray(taps, np.float64))
+        out = ctypes.c_void_p()
+        st = lib.mot_create(ctypes.cast(grid, ctypes.c_void_p), ctypes.cast(hh, ctypes.c_void_p),
+                            h, eps.ctypes.data, t.ctypes.data if t.size else None, int(t.size),
+                            PRECISIONS[precision], SCHEMES[scheme], int(block),
+                            ctypes.byref(out))
+        if st != MOT_OK:
+            raise MotError(st, lib.mot_last_error(None).decode())
+        self._h = out
+        self._lib = lib
+        info = self.info()
+        self.ell = info["ell"]
+        self.P = info["P"]
+
+    # -- helpers
+    def _check(self, st):
+        if st != MOT_OK:
+            raise MotError(st, self._lib.mot_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mot_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API
+    def set_excitation(self, E, stream=None):
+        if not _dtype_ok(E):
+            raise TypeError("E must be float64")
+        n = E.shape[0]
+        self._check(self._lib.mot_set_excitation(self._h, n, _ptr(E), _stream(stream)))
+
+    def plane_wave(self, k_hat, p_hat, f_c, sigma_t, t0, n_first, n_steps, out=None, stream=None):
+        if out is None:
+            out = np.zeros((n_steps, self.M, 3))
+        k = np.ascontiguousarray(k_hat, dtype=np.float64)
+        p = np.ascontiguousarray(p_hat, dtype=np.float64)
+        self._check(self._lib.mot_plane_wave(self._h, k.ctypes.data, p.ctypes.data, f_c, sigma_t,
+                                             t0, n_first, n_steps, _ptr(out), _stream(stream)))
+        return out
+
+    def march(self, n_steps, out="host", stream=None):
+        """March n_steps; out='host' returns a new numpy array, None keeps J on the
+        device, or pass a preallocated numpy array / torch tensor."""
+        if isinstance(out, str):
+            out = np.zeros((n_steps, self.M, 3))
+        if out is not None and not _dtype_ok(out):
+            raise TypeError("out must be float64")
+        self._check(self._lib.mot_march(self._h, n_steps, _ptr(out), _stream(stream)))
+        return out
+
+    def eval_history(self, J_hist, out=None, stream=None):
+        J = J_hist
+        if isinstance(J, np.ndarray):
+            J = np.ascontiguousarray(J, dtype=np.float64)
+        if out is None:
+            out = np.zeros((self.M, 3))
+        self._check(self._lib.mot_eval_history(self._h, J.shape[0], _ptr(J), _ptr(out),
+                                               _stream(stream)))
+        return out
+
+    def table(self, l0, n_lags):
+        W, V, U = self.shape
+        out = np.zeros((n_lags, 6, W, V, U))
+        self._check(self._lib.mot_get_table(self._h, l0, n_lags, out.ctypes.data))
+        return out
+
+    def spectrum(self, l):
+        Pu, Pv, Pw = self.P
+        out = np.zeros((6, Pw // 2 + 1, Pv // 2 + 1, Pu // 2 + 1))
+        self._check(self._lib.mot_get_spectrum(self._h, l, out.ctypes.data))
+        return out
+
+    def info(self):
+        ell = ctypes.c_int()
+        P = (ctypes.c_int * 3)()
+        nd = ctypes.c_int()
+        ln = ctypes.c_double()
+        fs = ctypes.c_int()
+        it = ctypes.c_int()
+        st = self._lib.mot_get_info(self._h, ctypes.byref(ell), ctypes.cast(P, ctypes.c_void_p),
+                                    ctypes.byref(nd), ctypes.byref(ln), ctypes.byref(fs),
+                                    ctypes.byref(it))
+        self._check(st)
+        return {"ell": ell.value, "P": tuple(P), "n_done": nd.value, "last_norm": ln.value,
+                "fail_step": fs.value, "last_cg_iters": it.value}
+
+    def set_profiling(self, enable=True):
+        self._check(self._lib.mot_set_profiling(self._h, 1 if enable else 0))
+
+    def stats(self):
+        st = Stats()
+        self._check(self._lib.mot_get_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def set_solver(self, tol=1e-13, max_iter=200, growth_limit=1e12):
+        self._check(self._lib.mot_set_solver(self._h, tol, max_iter, growth_limit))

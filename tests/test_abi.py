@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/mot.h declares (no GPU call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_03323_gb300 import build, mot
+    if not os.path.exists(mot.LIB_PATH):
+        build.build()
+    return mot.load_library()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "mot.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mot_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("mot_create", "mot_set_excitation", "mot_march", "mot_destroy"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_export():
+    from paper_2407_03323_gb300 import mot
+    assert sorted(mot.EXPORTS) == declared_symbols()
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    """Argument validation happens on the host: a non-cubic voxel, c dt != h and
+    eps_r < 1 are MOT_ERR_ARG with a message."""
+    out = ctypes.c_void_p()
+    eps = (ctypes.c_double * 8)(*([2.0] * 8))
+    grid = (ctypes.c_int * 3)(2, 2, 2)
+    h_bad = (ctypes.c_double * 3)(1.0, 1.0, 2.0)
+    st = lib.mot_create(ctypes.cast(grid, ctypes.c_void_p), ctypes.cast(h_bad, ctypes.c_void_p),
+                        1.0, ctypes.cast(eps, ctypes.c_void_p), None, 0, 0, 0, 0,
+                        ctypes.byref(out))
+    assert st == 1 and not out.value
+    assert b"cubes" in lib.mot_last_error(None)
+    h = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    st = lib.mot_create(ctypes.cast(grid, ctypes.c_void_p), ctypes.cast(h, ctypes.c_void_p),
+                        0.5, ctypes.cast(eps, ctypes.c_void_p), None, 0, 0, 0, 0,
+                        ctypes.byref(out))
+    assert st == 1 and b"dt" in lib.mot_last_error(None)
+    eps[3] = 0.5
+    st = lib.mot_create(ctypes.cast(grid, ctypes.c_void_p), ctypes.cast(h, ctypes.c_void_p),
+                        1.0, ctypes.cast(eps, ctypes.c_void_p), None, 0, 0, 0, 0,
+                        ctypes.byref(out))
+    assert st == 1 and b"eps_r" in lib.mot_last_error(None)

@@ -1,0 +1,209 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: the element tables of both sides are independent FP64 quadratures
+(~1e-14 of the largest element each), so tables agree to 1e-12 of the largest
+element; the FP64 march must match the oracle to a relative L2 of 1e-10 over all
+J_n; the FP32-history march must stay within 1e-5 relative L2 of the FP64 march.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mot():
+    from paper_2407_03323_gb300 import build, mot as m
+    if not os.path.exists(m.LIB_PATH):
+        build.build()
+    m.load_library()
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_table_matches_oracle_cube8(mot, cube8_oracle):
+    o = cube8_oracle
+    with mot.Context(o["cfg"]["eps_r"]) as ctx:
+        assert ctx.ell == o["ell"]
+        g = ctx.table(0, ctx.ell + 1)
+    G = o["G"]                                   # [l][c][dz][dy][dx]
+    assert g.shape == G.shape
+    assert np.abs(g - G).max() < 1e-12 * np.abs(G).max()
+
+
+def test_table_matches_oracle_sampled_offsets(mot):
+    """A 40^3 grid: the table at offsets up to 39 against the oracle's elements."""
+    from oracle import kernel_table as kt
+    N = 40
+    with mot.Context(wl.cube(N, 2.0), precision="fp32_history") as ctx:
+        ell = ctx.ell
+        g = ctx.table(0, ell + 1)
+    rng = np.random.default_rng(7)
+    offs = [(0, 0, 0), (1, 0, 0), (39, 39, 39), (39, 0, 0), (17, 3, 29)]
+    offs += [tuple(int(v) for v in rng.integers(0, N, 3)) for _ in range(12)]
+    for d in offs:
+        vol, face = kt.offset_elements(d, ell + 1)
+        comps = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+        for c, (a, b) in enumerate(comps):
+            ref = face[a, b] - (vol if a == b else 0.0)
+            got = g[:, c, d[2], d[1], d[0]]
+            assert np.abs(got - ref).max() < 1e-12 * max(np.abs(ref).max(), 1e-6), (d, c)
+
+
+def test_spectrum_matches_direct_dft(mot, cube8_oracle):
+    """Ghat_l(k) = sum_d G_l(d) exp(-2 pi i k.d/P) (App. A) at every octant bin, with
+    the oracle's table and the plain definition of the DFT."""
+    from oracle.march import g_block
+    o = cube8_oracle
+    N = 8
+    with mot.Context(o["cfg"]["eps_r"]) as ctx:
+        P = ctx.P[0]
+        for l in (1, 5, ctx.ell):
+            S = ctx.spectrum(l)                  # [6][Hw][Hv][Hu]
+            r = np.arange(-(N - 1), N)
+            dz, dy, dx = np.meshgrid(r, r, r, indexing="ij")
+            d = np.stack([dx, dy, dz], axis=-1)
+            B = g_block(o["G"], l, d)            # [.., 3, 3]
+            H = P // 2 + 1
+            k = np.arange(H)
+            ex = np.exp(-2j * np.pi * np.outer(k, r) / P)   # [k, d]
+            comps = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+            for c, (a, b) in enumerate(comps):
+                ref = np.einsum("zyx,az,by,cx->abc", B[..., a, b], ex, ex, ex)
+                assert np.abs(ref.imag).max() < 1e-12
+                assert np.abs(S[c] - ref.real).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_excitation_matches_oracle(mot):
+    from oracle import excitation
+    cfg = wl.config("sphere12")
+    p = cfg["pulse"]
+    with mot.Context(cfg["eps_r"]) as ctx:
+        E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"], 70, 12)
+    ref = excitation.tested_excitation(cfg["eps_r"], p, 12, n_first=70)
+    assert np.abs(E - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_history"])
+def test_history_matches_direct_sum(mot, cube8_oracle, precision):
+    """P_{n-1} = sum_l Z_l J_{n-l} through the FFT / ring / MAC path equals the
+    oracle's direct space-time sum (Eq. PnMOT) on random histories."""
+    from oracle import march
+    o = cube8_oracle
+    eps = o["cfg"]["eps_r"].copy()
+    eps[2:5, 1:7, 3] = 9.0                      # heterogeneous chi
+    taps = wl.fir_taps("hp9", 0.05)
+    rng = np.random.default_rng(11)
+    ell = o["ell"]
+    M = eps.size
+    Jh = rng.normal(size=(ell, M, 3))
+    with mot.Context(eps, taps, precision=precision) as ctx:
+        P = ctx.eval_history(Jh)
+    ref = march.history_at(o["G"], eps, taps, Jh, list(range(M)))
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert rel_l2(P, ref) < tol
+
+
+def test_history_sparse_sources_32(mot):
+    """32^3 grid (P = 64): a history supported on a few source voxels, compared at
+    sampled test voxels with the oracle's direct sum over those sources."""
+    from oracle import kernel_table as kt
+    from oracle.march import offsets_and_index
+    from oracle.spline import T_at_lag
+    N = 32
+    eps = wl.sphere(N, 12.0)
+    taps = wl.fir_taps("hp9", 1e-7 * N ** 3)
+    rng = np.random.default_rng(5)
+    with mot.Context(eps, taps) as ctx:
+        ell = ctx.ell
+        M = eps.size
+        active = np.nonzero(eps.reshape(-1) > 1)[0]
+        src = rng.choice(active, 6, replace=False)
+        Jh = np.zeros((ell, M, 3))
+        Jh[:, src, :] = rng.normal(size=(ell, len(src), 3))
+        P = ctx.eval_history(Jh)
+    idx = offsets_and_index(N, N, N)
+    e = eps.reshape(-1)
+    chi = (e - 1) / e
+    tests = list(rng.choice(active, 10, replace=False)) + list(src[:2])
+    cache = {}
+    for m in tests:
+        acc = np.zeros(3)
+        for s in src:
+            d = idx[m] - idx[s]
+            key = tuple(int(v) for v in np.abs(d))
+            if key not in cache:
+                cache[key] = kt.offset_elements(key, ell + 1)
+            vol, face = cache[key]
+            sg = np.sign(d)
+            G = face.copy()
+            for a in range(3):
+                for b in range(3):
+                    if a != b:
+                        G[a, b] = G[a, b] * sg[a] * sg[b]
+                G[a, a] = G[a, a] - vol
+            for l in range(1, ell + 1):
+                acc -= chi[m] * G[:, :, l] @ Jh[l - 1, s]
+        for l in range(1, ell + 1):
+            acc += (T_at_lag(l) / e[m] + (taps[l] if l < len(taps) else 0.0)) * Jh[l - 1, m]
+        assert np.abs(P[m] - acc).max() < 1e-11 * max(np.abs(acc).max(), 1e-3)
+
+
+def test_march_cube8_fp64_matches_oracle(mot, cube8_oracle):
+    o = cube8_oracle
+    with mot.Context(o["cfg"]["eps_r"], o["cfg"]["taps"]) as ctx:
+        ctx.set_excitation(o["E"])
+        J = ctx.march(o["E"].shape[0])
+        info = ctx.info()
+    assert info["n_done"] == o["E"].shape[0]
+    assert rel_l2(J, o["J"]) < 1e-10
+
+
+def test_march_cube8_fp32_history_close_to_fp64(mot, cube8_oracle):
+    o = cube8_oracle
+    with mot.Context(o["cfg"]["eps_r"], o["cfg"]["taps"], precision="fp32_history") as ctx:
+        ctx.set_excitation(o["E"])
+        J = ctx.march(o["E"].shape[0])
+    assert rel_l2(J, o["J"]) < 1e-5
+
+
+def test_march_fir_sphere_matches_oracle(mot):
+    """Sphere eps_r = 12 in 8^3 with the 9-tap linear-phase high-pass FIR (delta = 0.05),
+    excitation computed on each side independently."""
+    from oracle import excitation, kernel_table, march
+    from oracle.spline import num_lags
+    N = 8
+    eps = wl.sphere(N, 12.0)
+    taps = wl.fir_taps("hp9", 0.05)
+    p = wl.pulse(N, 12.0, k_hat=(1.0, 2.0, 2.0), p_hat=(0.0, 1.0, -1.0))
+    steps = 160
+    G, _, _ = kernel_table.octant_table(N, num_lags(N, N, N) + 1)
+    E = excitation.tested_excitation(eps, p, steps)
+    Jref = march.march(G, eps, taps, E)
+    with mot.Context(eps, taps) as ctx:
+        Eg = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"], 1, steps)
+        ctx.set_excitation(Eg)
+        J = ctx.march(steps)
+    assert rel_l2(J, Jref) < 1e-10
+
+
+def test_march_in_chunks_equals_one_call(mot, cube8_oracle):
+    o = cube8_oracle
+    E = o["E"][:96]
+    with mot.Context(o["cfg"]["eps_r"]) as ctx:
+        ctx.set_excitation(E)
+        J1 = ctx.march(96)
+    with mot.Context(o["cfg"]["eps_r"]) as ctx:
+        parts = []
+        for a in range(0, 96, 32):
+            ctx.set_excitation(E[a:a + 32])
+            parts.append(ctx.march(32))
+        J2 = np.concatenate(parts)
+    assert np.array_equal(J1, J2)
