@@ -217,8 +217,12 @@ __global__ void quad_kernel(const int3* __restrict__ triples, int ntriples,
             cL[2 * i + j] = make_cell(dp, dq, i, j, 0);
             cD[2 * i + j] = make_cell(dp, dq, i, j, 1);
         }
-    double smax = 0.0;
-    for (int i = 0; i < 4; ++i) smax = fmax(smax, hypot(cL[i].x1, cL[i].y1));
+    // the in-plane weight vanishes for s outside [smin, smax]
+    double smax = 0.0, smin = 1e300;
+    for (int i = 0; i < 4; ++i) {
+        smax = fmax(smax, hypot(cL[i].x1, cL[i].y1));
+        smin = fmin(smin, hypot(cL[i].x0, cL[i].y0));
+    }
     const double zk0 = dz - 1.0, zk1 = dz, zk2 = dz + 1.0;
     const double zmax = fmax(fabs(zk0), fabs(zk2));
     const double rmax = hypot(smax, zmax);
@@ -228,7 +232,7 @@ __global__ void quad_kernel(const int3* __restrict__ triples, int ntriples,
     if (lane == 0) {
         double* bp = sbp[wib];
         int n = 0;
-        bp[n++] = 0.0;
+        bp[n++] = smin;
         bp[n++] = smax;
         for (int i = 0; i < 4; ++i) {
             const Cell& c = cL[i];
@@ -242,7 +246,7 @@ __global__ void quad_kernel(const int3* __restrict__ triples, int ntriples,
             for (int e = 0; e < 3; ++e)
                 if (j > fabs(zks[e])) bp[n++] = sqrt((double)j * j - zks[e] * zks[e]);
         }
-        for (int i = 0; i < n; ++i) bp[i] = fmin(fmax(bp[i], 0.0), smax);
+        for (int i = 0; i < n; ++i) bp[i] = fmin(fmax(bp[i], smin), smax);
         sort_small(bp, n);
         int m = 1;
         for (int i = 1; i < n; ++i)
@@ -269,6 +273,7 @@ __global__ void quad_kernel(const int3* __restrict__ triples, int ntriples,
             double AL = 0.0, AD = 0.0;
             for (int i = 0; i < 4; ++i) { AL += arc_cell(s, cL[i]); AD += arc_cell(s, cD[i]); }
             const double oL = Ws * AL, oD = Ws * AD;
+            if (oL == 0.0 && oD == 0.0) continue;
             // diagonal face term: z-weight delta(z-dz+1) - 2 delta(z-dz) + delta(z-dz-1)
             {
                 const double zks[3] = {zk0, zk1, zk2};
