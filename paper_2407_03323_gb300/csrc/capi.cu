@@ -66,6 +66,8 @@ void free_all(mot_ctx* c) {
     for (double* p : dptrs) cudaFree(p);
     cudaFree(c->tab_l0);
     cudaFree(c->dstatus);
+    cudaFree(c->cg32);
+    cudaFree(c->active);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -112,6 +114,8 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
     if (!grid || !h || !eps_r || !out) return fail(MOT_ERR_ARG, "null argument");
     for (int a = 0; a < 3; ++a)
         if (grid[a] < 1 || grid[a] > 4096) return fail(MOT_ERR_ARG, "grid sizes must be in 1..4096");
+    if ((long long)grid[0] * grid[1] * grid[2] > (1LL << 30))
+        return fail(MOT_ERR_ARG, "at most 2^30 voxels");
     if (!(h[0] > 0) || h[0] != h[1] || h[0] != h[2])
         return fail(MOT_ERR_ARG, "voxels must be cubes (h[0] == h[1] == h[2] > 0)");
     if (!(dt > 0) || std::fabs(dt - h[0]) > 1e-12 * h[0])
@@ -177,6 +181,18 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         MOT_CUDA_TRY(cudaMalloc(&c->cg_r, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg_p, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg_q, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg32, sizeof(float) * 12 * M));
+        MOT_CUDA_TRY(cudaMemset(c->cg32, 0, sizeof(float) * 12 * M));
+        {
+            std::vector<int> act;
+            for (long long m = 0; m < M; ++m)
+                if (chi[m] > 0.0) act.push_back((int)m);
+            c->nact = (long long)act.size();
+            MOT_CUDA_TRY(cudaMalloc(&c->active, sizeof(int) * std::max<long long>(c->nact, 1)));
+            if (c->nact)
+                MOT_CUDA_TRY(cudaMemcpy(c->active, act.data(), sizeof(int) * c->nact,
+                                        cudaMemcpyHostToDevice));
+        }
         MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
         MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
         MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));

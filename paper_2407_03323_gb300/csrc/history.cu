@@ -47,76 +47,66 @@ struct MacGeom {
     long long nbins, noct;
 };
 
-// P^(kbins) = scale * sum_{l=l_lo}^{l_hi} Ghat_l(k) Jhat_{n-l}(k)  (+ add_in if given)
+// Phat(k) = scale * sum_{l=1}^{L} Ghat_l(k) Jhat_{n-l}(k) over all rfft bins.
+// A warp covers 8 consecutive octant bins (ku) x 4 mirrors: lane = mirror * 8 + j.
+// The 8 lanes of a mirror read 8 consecutive bins of a ring row; the kernel values of
+// the 8 bins ([lag][octant bin][6], 6 per bin) are one contiguous load shared by the
+// 4 mirror groups.  Ring slots are walked backwards from slot_first = (n-1) mod hring.
 template <typename R>
 __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
                                             const typename CT<R>::c* __restrict__ ring, int hring,
-                                            int n, int l_lo, int l_hi, MacGeom g, R scale,
+                                            int slot_first, int L, MacGeom g, R scale,
                                             typename CT<R>::c* __restrict__ phat) {
     typedef typename CT<R>::c C;
-    const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    typedef typename std::conditional<std::is_same<R, double>::value, double2, float2>::type R2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int mirror = lane >> 3, j = lane & 7;
+    const long long o = ((long long)blockIdx.x * (NT / 32) + warp) * 8 + j;
     if (o >= g.noct) return;
     const int ku = (int)(o % g.Hu);
     const int kv = (int)((o / g.Hu) % g.Hv);
     const int kw = (int)(o / ((long long)g.Hu * g.Hv));
     const bool mv = kv > 0 && 2 * kv < g.Pv;
     const bool mw = kw > 0 && 2 * kw < g.Pw;
-    long long bidx[4];
-    bool valid[4];
-    bidx[0] = ((long long)kw * g.Pv + kv) * g.Hu + ku;
-    bidx[1] = ((long long)kw * g.Pv + (g.Pv - kv)) * g.Hu + ku;
-    bidx[2] = ((long long)(g.Pw - kw) * g.Pv + kv) * g.Hu + ku;
-    bidx[3] = ((long long)(g.Pw - kw) * g.Pv + (g.Pv - kv)) * g.Hu + ku;
-    valid[0] = true;
-    valid[1] = mv;
-    valid[2] = mw;
-    valid[3] = mv && mw;
-    // sign of (xy, xz, yz) in each mirror
-    const R sxy[4] = {(R)1, (R)-1, (R)1, (R)-1};
-    const R sxz[4] = {(R)1, (R)1, (R)-1, (R)-1};
-    const R syz[4] = {(R)1, (R)-1, (R)-1, (R)1};
-    Acc<R> acc[4][3];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc[m][a].zero();
+    const bool fv = (mirror & 1) != 0, fw = (mirror & 2) != 0;
+    if ((fv && !mv) || (fw && !mw)) return;
+    const int kv2 = fv ? g.Pv - kv : kv;
+    const int kw2 = fw ? g.Pw - kw : kw;
+    const long long bidx = ((long long)kw2 * g.Pv + kv2) * g.Hu + ku;
+    const R sxy = fv ? (R)-1 : (R)1;
+    const R sxz = fw ? (R)-1 : (R)1;
+    const R syz = (fv != fw) ? (R)-1 : (R)1;
+    Acc<R> ax, ay, az;
+    ax.zero(); ay.zero(); az.zero();
     const long long slot_stride = 3 * g.nbins;
-    for (int l = l_lo; l <= l_hi; ++l) {
-        const R* gp = ghat + (long long)(l - 1) * 6 * g.noct + o;
-        const R gxx = gp[0], gyy = gp[g.noct], gzz = gp[2 * g.noct];
-        const R gxy = gp[3 * g.noct], gxz = gp[4 * g.noct], gyz = gp[5 * g.noct];
-        const long long slot = (((long long)(n - l)) % hring + hring) % hring;
-        const C* base = ring + slot * slot_stride;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            if (!valid[m]) continue;
-            const C x = base[bidx[m]];
-            const C y = base[g.nbins + bidx[m]];
-            const C z = base[2 * g.nbins + bidx[m]];
-            const R a = sxy[m] * gxy, b = sxz[m] * gxz, cc = syz[m] * gyz;
-            C ox, oy, oz;
-            ox.x = gxx * x.x + a * y.x + b * z.x;
-            ox.y = gxx * x.y + a * y.y + b * z.y;
-            oy.x = a * x.x + gyy * y.x + cc * z.x;
-            oy.y = a * x.y + gyy * y.y + cc * z.y;
-            oz.x = b * x.x + cc * y.x + gzz * z.x;
-            oz.y = b * x.y + cc * y.y + gzz * z.y;
-            acc[m][0].add(ox);
-            acc[m][1].add(oy);
-            acc[m][2].add(oz);
-        }
+    int slot = slot_first;
+    const R2* gp = reinterpret_cast<const R2*>(ghat + o * 6);
+    const long long gstep = g.noct * 3;   // in R2 units per lag
+#pragma unroll 2
+    for (int l = 1; l <= L; ++l) {
+        const R2 g01 = gp[0], g23 = gp[1], g45 = gp[2];
+        gp += gstep;
+        const C* base = ring + (long long)slot * slot_stride + bidx;
+        const C x = base[0];
+        const C y = base[g.nbins];
+        const C z = base[2 * g.nbins];
+        slot = slot == 0 ? hring - 1 : slot - 1;
+        const R gxx = g01.x, gyy = g01.y, gzz = g23.x;
+        const R a = sxy * g23.y, b = sxz * g45.x, cc = syz * g45.y;
+        C ox, oy, oz;
+        ox.x = gxx * x.x + a * y.x + b * z.x;
+        ox.y = gxx * x.y + a * y.y + b * z.y;
+        oy.x = a * x.x + gyy * y.x + cc * z.x;
+        oy.y = a * x.y + gyy * y.y + cc * z.y;
+        oz.x = b * x.x + cc * y.x + gzz * z.x;
+        oz.y = b * x.y + cc * y.y + gzz * z.y;
+        ax.add(ox);
+        ay.add(oy);
+        az.add(oz);
     }
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        if (!valid[m]) continue;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            C v = acc[m][a].get();
-            v.x *= scale;
-            v.y *= scale;
-            phat[a * g.nbins + bidx[m]] = v;
-        }
-    }
+    C v = ax.get(); v.x *= scale; v.y *= scale; phat[bidx] = v;
+    v = ay.get(); v.x *= scale; v.y *= scale; phat[g.nbins + bidx] = v;
+    v = az.get(); v.x *= scale; v.y *= scale; phat[2 * g.nbins + bidx] = v;
 }
 
 MacGeom geom(const mot_ctx* c) {
@@ -178,8 +168,10 @@ void history_step(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t ev_fwd, cudaEve
     }
     if (ev_fwd) MOT_CUDA_TRY(cudaEventRecord(ev_fwd, s));
     const R scale = (R)(1.0 / ((double)c->ax[0].P * c->ax[1].P * c->ax[2].P));
-    k_mac<R><<<(int)((c->noct + NT - 1) / NT), NT, 0, s>>>(hb.ghat, hb.jhat_ring, c->hring, n, 1,
-                                                           c->ell, geom(c), scale, hb.phat);
+    const long long nblk = (c->noct + 8 * (NT / 32) - 1) / (8 * (NT / 32));
+    k_mac<R><<<(int)nblk, NT, 0, s>>>(hb.ghat, hb.jhat_ring, c->hring,
+                                      (int)slot_index(n - 1, c->hring), c->ell, geom(c), scale,
+                                      hb.phat);
     MOT_LAUNCH_CHECK();
     c->stats.launches += 1;
     c->stats.mac_launches += 1;

@@ -97,6 +97,9 @@ struct mot_ctx {
     double* cg_r = nullptr;
     double* cg_p = nullptr;
     double* cg_q = nullptr;
+    float* cg32 = nullptr;       // FP32 inner CG vectors r, p, q, e ([4][3][M])
+    int* active = nullptr;       // voxels with chi > 0
+    long long nact = 0;
     double* red = nullptr;       // reduction scratch
     int* dstatus = nullptr;      // [0] cg iterations of last step, [1] flags
     double* norms = nullptr;     // per-step ||J_n||^2 of the current call

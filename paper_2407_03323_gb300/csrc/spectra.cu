@@ -63,6 +63,17 @@ __global__ void pass_mid(const double* __restrict__ in, int n, int F, long long 
     out[i] = acc;
 }
 
+// [6][noct] (component-major) -> [noct][6] in the history precision
+template <typename R>
+__global__ void interleave_kernel(const double* __restrict__ src, long long noct,
+                                  R* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * noct) return;
+    const long long o = i / 6;
+    const int cc = (int)(i % 6);
+    dst[i] = (R)src[cc * noct + o];
+}
+
 template <typename R>
 __global__ void store_kernel(const double* __restrict__ src, long long n, double scale,
                              R* __restrict__ dst) {
@@ -140,27 +151,25 @@ void make_scratch(mot_ctx* c, Scratch& sc) {
 
 namespace mot {
 
-// ghat[lag-1][cc][Hw][Hv][Hu] for lags 1..ell, in the history precision, unnormalised
+// ghat[lag-1][octant bin][6] for lags 1..ell, in the history precision, unnormalised
 void compute_spectra(mot_ctx* c) {
     TrigTables tt;
     Scratch sc;
     make_tables(c, tt);
     make_scratch(c, sc);
     double* tmp = nullptr;
-    MOT_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * c->noct));
+    MOT_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * c->noct * 6));
     try {
         for (int l = 1; l <= c->ell; ++l) {
-            for (int cc = 0; cc < 6; ++cc) {
-                const long long off = ((long long)(l - 1) * 6 + cc) * c->noct;
-                if (c->precision == MOT_FP64) {
-                    spectrum_one(c, tt, sc, l, cc, c->h64.ghat + off);
-                } else {
-                    spectrum_one(c, tt, sc, l, cc, tmp);
-                    store_kernel<float><<<nblk(c->noct, 256), 256, 0, c->stream>>>(
-                        tmp, c->noct, 1.0, c->h32.ghat + off);
-                    MOT_LAUNCH_CHECK();
-                }
-            }
+            for (int cc = 0; cc < 6; ++cc) spectrum_one(c, tt, sc, l, cc, tmp + cc * c->noct);
+            const long long off = (long long)(l - 1) * 6 * c->noct;
+            if (c->precision == MOT_FP64)
+                interleave_kernel<double><<<nblk(6 * c->noct, 256), 256, 0, c->stream>>>(
+                    tmp, c->noct, c->h64.ghat + off);
+            else
+                interleave_kernel<float><<<nblk(6 * c->noct, 256), 256, 0, c->stream>>>(
+                    tmp, c->noct, c->h32.ghat + off);
+            MOT_LAUNCH_CHECK();
         }
         MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     } catch (...) {
