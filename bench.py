@@ -3,14 +3,19 @@
 Workload (default): dielectric sphere eps_r = 12 voxelised in a 104^3 grid
 (1,124,864 voxels of the bounding grid, 589,344 inside, 3 components), c dt = h,
 9-tap linear-phase high-pass FIR regularisation with delta = 1e-7 * 104^3, single
-x-polarised +z modulated-Gaussian plane wave.  A "step" is one time step of the march:
-the forward FFT of J_{n-1}, the lag multiply-accumulate over the spectral ring, the
-inverse FFT, the FIR epilogue and the CG solve of Z_0.
+x-polarised +z modulated-Gaussian plane wave (the pulse peaks inside the timed window).
+
+Variants: FP32-history and FP64 with the blocked temporal scheme (block B = 16, levels
+16..128), and the plain FP64 direct march for comparison.  A bench "step" is one pass
+of every row of the hot path: for the blocked scheme one period of the block schedule
+(S_max = 128 time steps, in which every level fires), for the direct scheme one time
+step.  Each time step runs the forward FFT of J_{n-1}, the far-lag block products due
+at that step, the near-lag MAC, the inverse FFT, the FIR epilogue and the Z_0 solve.
 
 Metric: voxel-timesteps/s = (bounding-grid voxels) x (time steps) / march time.
-The headline value is the FP32-history march; the FP64 march is reported alongside.
-Inputs (the excitation of every timed step) are resident in HBM before the timed
-region; the spectral ring (tens of GB) is far larger than L2, so no flush is needed.
+The headline value is the first variant (FP32-history, blocked).  Inputs (the
+excitation of every timed time step) are resident in HBM before the timed region; the
+spectral ring (tens of GB) is far larger than L2, so no flush is needed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -37,11 +42,13 @@ REF_SAMPLE_N = 10          # oracle sample grid (its direct sum is O(M^2) per st
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=24)
-    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "fp32_history", "fp64"])
     ap.add_argument("--config", default=CONFIG_NAME)
+    ap.add_argument("--scheme", default="blocked", choices=["blocked", "direct"])
+    ap.add_argument("--block", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -119,22 +126,49 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def mac_bytes_per_launch(ctx, precision):
-    """Algorithmic bytes of one direct lag-MAC launch: every lag reads the real kernel
-    spectrum once per octant bin (6 values) and the three complex spectra of J at every
-    rfft bin; the result is written once per rfft bin (3 complex values)."""
-    s = 8 if precision == "fp64" else 4
+def geometry(ctx):
     Pu, Pv, Pw = ctx.P
     Hu, Hv, Hw = Pu // 2 + 1, Pv // 2 + 1, Pw // 2 + 1
-    noct = Hu * Hv * Hw
-    nbins = Pw * Pv * Hu
-    L = ctx.ell
-    return L * (6 * s * noct + 6 * s * nbins) + 6 * s * nbins
+    return Hu * Hv * Hw, Pw * Pv * Hu
 
 
-def profile_traffic(precision):
-    """DRAM bytes per k_mac launch from the committed ncu summary, if recorded."""
-    p = os.path.join(ROOT, "profiles", "k_mac_sphere104.txt")
+def mac_bytes_per_launch(ctx, precision, lags, with_acc):
+    """Algorithmic bytes of one lag-MAC launch over `lags` lags: every lag reads the real
+    kernel spectrum once per octant bin (6 values) and the three complex spectra of J
+    at every rfft bin; the result (3 complex) is written once per rfft bin; with the
+    blocked scheme the step's far-lag accumulator is read and cleared (2 x 3 complex)."""
+    s = 8 if precision == "fp64" else 4
+    noct, nbins = geometry(ctx)
+    b = lags * (6 * s * noct + 6 * s * nbins) + 6 * s * nbins
+    if with_acc:
+        b += 2 * 6 * s * nbins
+    return b
+
+
+def far_bytes_per_period(ctx, precision):
+    """Algorithmic bytes of every block Toeplitz launch of one period (each level S
+    fires S_max / S times): the window of min(2S - 1, ell) past spectra (3 complex per
+    bin), the level's temporal kernel spectra (S + 1 frequencies x 6 complex per
+    octant bin), and a read-modify-write of S future accumulators (3 complex per bin)."""
+    c = 16 if precision == "fp64" else 8
+    noct, nbins = geometry(ctx)
+    levels = ctx.levels
+    if not levels:
+        return 0, 0
+    smax = levels[-1]
+    total, launches = 0, 0
+    for S in levels:
+        lmax = min(2 * S - 1, ctx.ell)
+        per = 3 * c * nbins * lmax + (S + 1) * 6 * c * noct + 2 * S * 3 * c * nbins
+        total += per * (smax // S)
+        launches += smax // S
+    return total, launches
+
+
+def profile_traffic(config, precision, kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if recorded
+    for this workload."""
+    p = os.path.join(ROOT, "profiles", "%s_%s.txt" % (kernel, config))
     if not os.path.exists(p):
         return None
     key = "traffic_bytes_per_launch_%s:" % precision
@@ -149,90 +183,137 @@ def profile_traffic(precision):
 
 # ------------------------------------------------------------------ our arm
 
-def run_ours(args, rank, world):
+def march_timed(ctx, torch, stream, E, n_steps, dev, world):
+    """Time n_steps of mot_march (excitation staged from the device tensor E)."""
+    ctx.set_excitation(E, stream=stream)
+    ctx.set_profiling(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        ctx.march(n_steps, out=None, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, clk.summary()
+
+
+def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_e2e):
     import torch
     from paper_2407_03323_gb300 import Context
+    eps, taps, p = cfg["eps_r"], cfg["taps"], cfg["pulse"]
+    M = eps.size
+    t_setup = time.time()
+    ctx = Context(eps, taps, precision=prec, scheme=scheme, block=block)
+    setup_s = time.time() - t_setup
+    stream = torch.cuda.current_stream()
+    # a bench step: one time step (direct), one period of the block schedule (blocked)
+    per = ctx.levels[-1] if (scheme == "blocked" and ctx.levels) else 1
+    n_warm, n_time = warmup * per, steps * per
+    # warm-up marches the pulse's leading edge; the timed steps get the pulse itself
+    Ew = torch.zeros((min(n_warm, per), M, 3), dtype=torch.float64, device="cuda")
+    done = 0
+    while done < n_warm:
+        k = min(per, n_warm - done)
+        ctx.set_excitation(Ew[:k], stream=stream)
+        ctx.march(k, out=None, stream=stream)
+        done += k
+    del Ew
+    E = torch.empty((n_time, M, 3), dtype=torch.float64, device="cuda")
+    t0 = p["t0"] + n_warm           # the pulse enters at the start of the timed window
+    ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], t0, n_warm + 1, n_time,
+                   out=E, stream=stream)
+    torch.cuda.synchronize()
+    ms, clocks = march_timed(ctx, torch, stream, E, n_time, dev, world)
+    st = ctx.stats()
+    info = ctx.info()
+    peak, peak_kind = measured_peaks()
+    # dominant kernel of the history evaluation
+    mac_lags = min(block - 1, ctx.ell) if scheme == "blocked" else ctx.ell
+    mac_b = mac_bytes_per_launch(ctx, prec, mac_lags, scheme == "blocked")
+    mac_ms = st["ms_mac"] / max(st["mac_launches"], 1)
+    cands = [("k_mac", mac_b, mac_ms, st["ms_mac"])]
+    if scheme == "blocked" and st["far_launches"]:
+        fb, fl = far_bytes_per_period(ctx, prec)
+        periods = st["far_launches"] / max(fl, 1)
+        far_bytes_launch = fb / max(fl, 1)
+        far_ms = st["ms_far"] / max(st["far_launches"], 1)
+        cands.append(("k_far", far_bytes_launch, far_ms, st["ms_far"]))
+    name, b_launch, ms_launch, _ = max(cands, key=lambda x: x[3])
+    achieved = b_launch / (ms_launch * 1e-3) / 1e9
+    hist_ms = st["ms_fft_fwd"] + st["ms_far"] + st["ms_mac"] + st["ms_fft_inv"]
+    out = {
+        "scheme": scheme, "block": block if scheme == "blocked" else None,
+        "time_steps_per_bench_step": per,
+        "value": world * M * n_time / (ms * 1e-3),
+        "ms_per_step": ms / steps, "ms_per_time_step": ms / n_time,
+        "setup_s": setup_s, "launches": st["launches"],
+        "cg_inner_iters_per_time_step": st["cg_iters"] / max(st["steps"], 1),
+        "phase_ms_per_time_step": {k: st["ms_" + k] / max(st["steps"], 1)
+                                   for k in ("fft_fwd", "far", "mac", "fft_inv", "solve")},
+        "history_ms_per_time_step": hist_ms / max(st["steps"], 1),
+        "roofline": {"bound": "hbm" if prec == "fp32_history" else "fp64-alu (hbm shown)",
+                     "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": profile_traffic(args.config, prec, name),
+                     "algorithmic_bytes_per_launch": b_launch},
+        "clocks": clocks, "ell": info["ell"], "P": list(info["P"]), "levels": ctx.levels,
+    }
+    e2e = None
+    if want_e2e:
+        k = per                                  # one bench step through host buffers
+        Eh = torch.empty((k, M, 3), dtype=torch.float64).pin_memory()
+        Eh.copy_(E[:k].cpu())
+        Jh = torch.empty((k, M, 3), dtype=torch.float64).pin_memory()
+        del E
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t_0 = time.perf_counter()
+        ctx.set_excitation(Eh, stream=stream)
+        ctx.march(k, out=Jh, stream=stream)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t_0
+        if world > 1:
+            t = torch.tensor([sec], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            sec = float(t.item())
+        e2e = {"value": world * M * k / sec, "unit": "voxel-timesteps/s",
+               "h2d_bytes_per_step": M * 3 * 8 * per, "d2h_bytes_per_step": M * 3 * 8 * per,
+               "variant": "%s/%s" % (prec, scheme)}
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out, e2e
+
+
+def run_ours(args, rank, world):
+    import torch
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     cfg = wl.config(args.config)
-    eps, taps, p = cfg["eps_r"], cfg["taps"], cfg["pulse"]
-    M = eps.size
-    precisions = ["fp32_history", "fp64"] if args.precision == "both" else [args.precision]
-    results = {}
-    e2e = None
-    for prec in precisions:
-        t_setup = time.time()
-        ctx = Context(eps, taps, precision=prec)
-        setup_s = time.time() - t_setup
-        stream = torch.cuda.current_stream()
-        W, K = args.warmup, args.steps
-        E = torch.empty((W + K, M, 3), dtype=torch.float64, device="cuda")
-        ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"], 1, W + K, out=E,
-                       stream=stream)
-        ctx.set_excitation(E, stream=stream)
-        torch.cuda.synchronize()
-        ctx.march(W, out=None, stream=stream)
-        torch.cuda.synchronize()
-        ctx.set_profiling(True)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        with ClockSampler(dev) as clk:
-            ev0.record(stream)
-            ctx.march(K, out=None, stream=stream)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        st = ctx.stats()
-        info = ctx.info()
-        mac_ms = st["ms_mac"] / max(st["mac_launches"], 1)
-        bytes_mac = mac_bytes_per_launch(ctx, prec)
-        peak, peak_kind = measured_peaks()
-        achieved = bytes_mac / (mac_ms * 1e-3) / 1e9
-        results[prec] = {
-            "value": world * M * K / (ms * 1e-3),
-            "ms_per_step": ms / K,
-            "setup_s": setup_s,
-            "launches": st["launches"],
-            "cg_iters_per_step": st["cg_iters"] / max(st["steps"], 1),
-            "phase_ms_per_step": {k: st["ms_" + k] / max(st["steps"], 1)
-                                  for k in ("fft_fwd", "mac", "fft_inv", "solve")},
-            "roofline": {"bound": "hbm", "kernel": "k_mac", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": profile_traffic(prec),
-                         "algorithmic_bytes_per_launch": bytes_mac},
-            "clocks": clk.summary(),
-            "ell": info["ell"], "P": list(info["P"]),
-        }
-        # end-to-end through the public API with host buffers (first precision only)
-        if e2e is None and not args.no_e2e:
-            Eh = torch.empty((K, M, 3), dtype=torch.float64).pin_memory()
-            Eh.copy_(E[W:W + K].cpu())
-            Jh = torch.empty((K, M, 3), dtype=torch.float64).pin_memory()
-            del E
-            torch.cuda.synchronize()
-            if world > 1:
-                torch.distributed.barrier()
-            t0 = time.perf_counter()
-            ctx.set_excitation(Eh, stream=stream)
-            ctx.march(K, out=Jh, stream=stream)
-            torch.cuda.synchronize()
-            sec = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([sec], device="cuda")
-                torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-                sec = float(t.item())
-            e2e = {"value": world * M * K / sec, "unit": "voxel-timesteps/s",
-                   "h2d_bytes_per_step": M * 3 * 8, "d2h_bytes_per_step": M * 3 * 8,
-                   "precision": prec}
-        ctx.close()
-        torch.cuda.empty_cache()
+    variants = []
+    precs = ["fp32_history", "fp64"] if args.precision == "both" else [args.precision]
+    for prec in precs:
+        variants.append((prec, args.scheme, args.block))
+    if args.precision == "both" and args.scheme == "blocked":
+        variants.append(("fp64", "direct", 0))     # the plain FP64 march, for comparison
+    results, e2e = {}, None
+    for prec, scheme, block in variants:
+        # the plain direct FP64 march is slow: time a few single steps
+        steps, warm = (args.steps, args.warmup)
+        if scheme == "direct" and args.scheme == "blocked":
+            steps, warm = 8, 3
+        r, e = run_variant(args, cfg, prec, scheme, block, dev, world, steps, warm,
+                           want_e2e=(e2e is None and not args.no_e2e))
+        results["%s/%s" % (prec, scheme)] = r
+        e2e = e2e or e
     return results, e2e
 
 
@@ -286,34 +367,39 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     results, e2e = run_ours(args, rank, world)
-    head = results.get("fp32_history") or results.get("fp64")
-    head_prec = "fp32_history" if "fp32_history" in results else "fp64"
+    head_key = next(iter(results))
+    head = results[head_key]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample(24, 2)
     if rank != 0:
         return
     M = wl.config(args.config)["eps_r"].size
+    prec = head_key.split("/")[0]
     line = {
         "metric": "voxel-timesteps/s", "value": head["value"], "unit": "voxel-timesteps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 history (FFT, spectra, lag MAC) + f64 (elements, FIR, CG)"
-                 if head_prec == "fp32_history" else "f64",
+        "dtype": "f32 history (FFT, spectra, lag products) + f64 (elements, FIR, CG residual)"
+                 if prec == "fp32_history" else "f64",
         "data": "synthetic",
         "config": {"workload": "sphere eps_r=12, %d^3 voxels (%d), c dt = h, hp9 FIR "
                                "delta=1e-7*M, +z x-polarised modulated Gaussian plane wave"
                                % (round(M ** (1 / 3)), M),
-                   "history": "direct spectral lag sum (all %d lags per step)" % head["ell"],
-                   "P": head["P"], "l2_flush": "inputs larger than L2 (spectral ring)",
+                   "variant": head_key,
+                   "step": ("one period of the block schedule = %d time steps"
+                            % head["time_steps_per_bench_step"])
+                           if head["time_steps_per_bench_step"] > 1 else "one time step",
+                   "levels": head["levels"], "P": head["P"], "ell": head["ell"],
+                   "l2_flush": "inputs larger than L2 (spectral ring)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": head["roofline"],
         "clocks": head["clocks"],
         "gpu_launches": head["launches"],
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "precisions": results,
+        "variants": results,
     }
     print(json.dumps(line))
 

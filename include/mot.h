@@ -137,6 +137,28 @@ mot_status mot_eval_history(mot_ctx* ctx, int n_hist, const double* J_hist, doub
                             void* stream);
 
 /*
+ * mot_adjoint - gradient of an objective O(J_1 .. J_N) with respect to eps_r per voxel,
+ * by the adjoint march: the transposed system of Eq. MatrixEquation solved backwards
+ * in time, Z_0^T lambda_n = g_n - sum_{l>=1} Z_l^T lambda_{n+l}, n = N .. 1, with
+ * g_n = dO/dJ_n and Z_l^T lambda = (T(l)/eps + delta_l) lambda - G_l * (chi lambda)
+ * (G_l is symmetric).  The gradient is
+ *     dO/deps_m = (1/eps_m^2) sum_n lambda_{n,m} . (1/chi_m) sum_l (T(l) + delta_l) J_{n-l,m},
+ * the chi-derivative of the forward rows (Eq. Z, Eq. E) simplified with the forward
+ * equation itself; it is defined for voxels with eps_m > 1 and set to 0 where eps_m = 1.
+ *  n_steps   N
+ *  J         [N][M][3] forward currents J_1 .. J_N (from mot_march; host or device)
+ *  dO_dJ     [N][M][3] g_n (host or device)
+ *  grad_eps  [M] output (host or device)
+ *  lambda    [N][M][3] optional output of lambda_1 .. lambda_N, or NULL
+ *  stream    cudaStream_t or NULL
+ * The march state is reset before and after; the same context (precision, history
+ * scheme, FIR taps, solver settings) serves forward and adjoint.
+ * Errors: MOT_ERR_ARG, MOT_ERR_OOM, MOT_ERR_NOT_CONVERGED, MOT_ERR_CUDA.
+ */
+mot_status mot_adjoint(mot_ctx* ctx, int n_steps, const double* J, const double* dO_dJ,
+                       double* grad_eps, double* lambda, void* stream);
+
+/*
  * mot_get_table - copy interaction elements G_l^{ab}(d) of lags l0..l0+n_lags-1 on
  * the octant d in [0,U-1]x[0,V-1]x[0,W-1] to host memory.
  *  out  host pointer, [n_lags][6][W][V][U] doubles, component order xx, yy, zz,
@@ -162,8 +184,12 @@ mot_status mot_get_spectrum(mot_ctx* ctx, int l, double* out);
 mot_status mot_get_info(const mot_ctx* ctx, int* ell, int P[3], int* n_done,
                         double* last_norm, int* fail_step, int* last_cg_iters);
 
-/* Set per-step solver/monitor parameters (defaults: tol 1e-13, max_iter 200,
- * growth_limit 1e12 times the largest norm seen).  tol is relative to ||rhs||. */
+/* Set per-step solver/monitor parameters.  tol: the FP64 residual of the Z_0 solve
+ * must fall below tol ||rhs / chi|| (default 1e-13 for MOT_FP64, 1e-10 for
+ * MOT_FP32_HISTORY, whose history already carries ~1e-7 relative error); max_iter:
+ * cap on the inner (FP32) iterations per step (default 200); growth_limit: a step
+ * whose ||J_n|| exceeds growth_limit times the largest norm seen so far is reported
+ * as MOT_ERR_UNSTABLE (default 1e12). */
 mot_status mot_set_solver(mot_ctx* ctx, double tol, int max_iter, double growth_limit);
 
 /* Counters of mot_march calls since the last mot_set_profiling (or creation).
@@ -171,15 +197,19 @@ mot_status mot_set_solver(mot_ctx* ctx, double tol, int max_iter, double growth_
  *  mac_launches  of which lag multiply-accumulate kernels
  *  steps         time steps marched
  *  cg_iters      total CG iterations
+ *  far_launches  of which block Toeplitz (temporal FFT) kernels, blocked scheme
  *  ms_*          summed CUDA-event durations of the phases, recorded on the stream
- *                mot_march ran on, only while profiling is enabled:
- *                forward FFT of J_{n-1}, lag MAC, inverse FFT, rhs + CG solve       */
+ *                mot_march ran on, only while profiling is enabled: forward FFT of
+ *                J_{n-1}, far-lag block products (blocked scheme), near-lag MAC,
+ *                inverse FFT, rhs + solve                                          */
 typedef struct {
     long long launches;
     long long mac_launches;
+    long long far_launches;
     long long steps;
     long long cg_iters;
     double ms_fft_fwd;
+    double ms_far;
     double ms_mac;
     double ms_fft_inv;
     double ms_solve;

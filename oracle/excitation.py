@@ -16,12 +16,13 @@ def incident(tau, f_c, sigma_t):
     return np.sin(2.0 * np.pi * f_c * tau) * np.exp(-tau * tau / (2.0 * sigma_t * sigma_t))
 
 
-def tested_excitation(eps_r, pulse, n_steps, n_first=1, npts=8):
+def tested_excitation(eps_r, pulse, n_steps, n_first=1, npts=8, with_chi=True):
     """E[n, m, b] for n = n_first .. n_first + n_steps - 1 (1-based times, t = n dt),
     m = u + U (v + V w) (Sec. 2.2, 0-based), b = x, y, z.  Returns an array of shape
-    (n_steps, M, 3)."""
+    (n_steps, M, 3).  with_chi=False returns the voxel-averaged incident field e_n
+    itself (E_n = chi e_n)."""
     W, V, U = eps_r.shape
-    chi = (eps_r - 1.0) / eps_r
+    chi = (eps_r - 1.0) / eps_r if with_chi else np.ones_like(eps_r)
     xg, wg = np.polynomial.legendre.leggauss(npts)
     off = 0.5 * xg            # offsets inside a unit voxel about its centre
     wo = 0.5 * wg

@@ -59,6 +59,7 @@ template <typename R> void alloc_history(mot_ctx* c) { mot::history_alloc<R>(c);
 
 void free_all(mot_ctx* c) {
     for (int a = 0; a < 3; ++a) mot::fft_free_axis(c->ax[a]);
+    for (int k = 0; k < 8; ++k) mot::fft_free_axis(c->lev_fft[k]);
     mot::history_free<double>(c);
     mot::history_free<float>(c);
     double* dptrs[] = {c->eps, c->chi, c->cg_diag, c->J, c->rhs, c->cg_r, c->cg_p,
@@ -68,6 +69,9 @@ void free_all(mot_ctx* c) {
     cudaFree(c->dstatus);
     cudaFree(c->cg32);
     cudaFree(c->active);
+    cudaFree(c->nmask);
+    cudaFree(c->diag32);
+    cudaFree(c->vfac);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -84,10 +88,9 @@ void reset_state(mot_ctx* c, cudaStream_t s) {
     c->fail_step = 0;
 }
 
-void history_for(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t e1 = nullptr,
-                 cudaEvent_t e2 = nullptr) {
-    if (c->precision == MOT_FP64) mot::history_step<double>(c, n, s, e1, e2);
-    else mot::history_step<float>(c, n, s, e1, e2);
+void history_for(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+    if (c->precision == MOT_FP64) mot::history_step<double>(c, n, s, ev);
+    else mot::history_step<float>(c, n, s, ev);
 }
 
 void ensure_events(mot_ctx* c, size_t n) {
@@ -124,8 +127,10 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         return fail(MOT_ERR_ARG, "n_taps must be 0..64 and fir_taps non-null when n_taps > 0");
     if (precision != MOT_FP64 && precision != MOT_FP32_HISTORY)
         return fail(MOT_ERR_ARG, "unknown precision");
-    if (scheme != MOT_HISTORY_DIRECT)
+    if (scheme != MOT_HISTORY_DIRECT && scheme != MOT_HISTORY_BLOCKED)
         return fail(MOT_ERR_ARG, "unknown history scheme");
+    if (scheme == MOT_HISTORY_BLOCKED && (block < 2 || (block & (block - 1)) != 0))
+        return fail(MOT_ERR_ARG, "block must be a power of two >= 2 for the blocked scheme");
     const long long M = (long long)grid[0] * grid[1] * grid[2];
     for (long long m = 0; m < M; ++m)
         if (!(eps_r[m] >= 1.0) || !std::isfinite(eps_r[m]))
@@ -140,6 +145,9 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
     c->block = block;
     c->n_taps = n_taps;
     c->taps.assign(fir_taps, fir_taps + n_taps);
+    // per-step solve tolerance: the FP32-history variant's history carries ~1e-7 relative
+    // error, so 1e-10 on the FP64 residual is far below it; FP64 solves to 1e-13
+    c->tol = precision == MOT_FP64 ? 1e-13 : 1e-10;
     // Eq. Ell with h = c dt = 1
     c->ell = (int)std::floor(std::sqrt((double)c->U * c->U + (double)c->V * c->V +
                                        (double)c->W * c->W)) + 2;
@@ -174,6 +182,10 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         if (precision == MOT_FP64) alloc_history<double>(c);
         else alloc_history<float>(c);
         mot::compute_spectra(c);
+        if (scheme == MOT_HISTORY_BLOCKED) {
+            if (precision == MOT_FP64) mot::level_spectra<double>(c);
+            else mot::level_spectra<float>(c);
+        }
         // marching state
         c->jring = std::max(n_taps, 4) + 1;
         MOT_CUDA_TRY(cudaMalloc(&c->J, sizeof(double) * 3 * M * c->jring));
@@ -181,19 +193,51 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         MOT_CUDA_TRY(cudaMalloc(&c->cg_r, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg_p, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg_q, sizeof(double) * 3 * M));
-        MOT_CUDA_TRY(cudaMalloc(&c->cg32, sizeof(float) * 12 * M));
-        MOT_CUDA_TRY(cudaMemset(c->cg32, 0, sizeof(float) * 12 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg32, sizeof(float) * 16 * M));
+        MOT_CUDA_TRY(cudaMemset(c->cg32, 0, sizeof(float) * 16 * M));
         {
-            std::vector<int> act;
-            for (long long m = 0; m < M; ++m)
-                if (chi[m] > 0.0) act.push_back((int)m);
+            std::vector<int> act, nm;
+            for (long long m = 0; m < M; ++m) {
+                if (!(chi[m] > 0.0)) continue;
+                act.push_back((int)m);
+                const int u = (int)(m % c->U), v = (int)((m / c->U) % c->V),
+                          w = (int)(m / ((long long)c->U * c->V));
+                int mask = 0;
+                for (int ez = -1; ez <= 1; ++ez)
+                    for (int ey = -1; ey <= 1; ++ey)
+                        for (int ex = -1; ex <= 1; ++ex) {
+                            const bool in = u + ex >= 0 && u + ex < c->U && v + ey >= 0 &&
+                                            v + ey < c->V && w + ez >= 0 && w + ez < c->W;
+                            if (in) mask |= 1 << ((ez + 1) * 9 + (ey + 1) * 3 + (ex + 1));
+                        }
+                nm.push_back(mask);
+            }
             c->nact = (long long)act.size();
-            MOT_CUDA_TRY(cudaMalloc(&c->active, sizeof(int) * std::max<long long>(c->nact, 1)));
-            if (c->nact)
+            const size_t na = std::max<size_t>(act.size(), 1);
+            MOT_CUDA_TRY(cudaMalloc(&c->active, sizeof(int) * na));
+            MOT_CUDA_TRY(cudaMalloc(&c->nmask, sizeof(int) * na));
+            if (c->nact) {
                 MOT_CUDA_TRY(cudaMemcpy(c->active, act.data(), sizeof(int) * c->nact,
                                         cudaMemcpyHostToDevice));
+                MOT_CUDA_TRY(cudaMemcpy(c->nmask, nm.data(), sizeof(int) * c->nact,
+                                        cudaMemcpyHostToDevice));
+            }
+            std::vector<float> d32(M);
+            std::vector<double> vf(4 * M);
+            for (long long m = 0; m < M; ++m) {
+                d32[m] = (float)dg[m];
+                vf[m] = 0.5 / e[m];
+                vf[M + m] = chi[m] > 0.0 ? 1.0 / chi[m] : 0.0;
+                vf[2 * M + m] = 1.0 / (0.5 / e[m] + d0);
+                vf[3 * M + m] = chi[m];
+            }
+            MOT_CUDA_TRY(cudaMalloc(&c->diag32, sizeof(float) * M));
+            MOT_CUDA_TRY(cudaMalloc(&c->vfac, sizeof(double) * 4 * M));
+            MOT_CUDA_TRY(cudaMemcpy(c->diag32, d32.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
+            MOT_CUDA_TRY(cudaMemcpy(c->vfac, vf.data(), sizeof(double) * 4 * M, cudaMemcpyHostToDevice));
         }
         MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
+        if (c->nact) mot::chebyshev_setup(c);
         MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
         MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
         reset_state(c, c->stream);
@@ -284,19 +328,19 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
         if (J_out && !dev_out && !c->outbuf)
             MOT_CUDA_TRY(cudaMalloc(&c->outbuf, sizeof(double) * 3 * c->M));
         MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
-        if (c->profiling) ensure_events(c, 5 * (size_t)n_steps);
+        if (c->profiling) ensure_events(c, 6 * (size_t)n_steps);
         for (int i = 0; i < n_steps; ++i) {
             const int n = c->n_done + 1 + i;
             const double* En = nullptr;
             if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count)
                 En = c->Estage + (long long)(n - c->E_first) * 3 * c->M;
-            cudaEvent_t* ev = c->profiling ? &c->events[5 * (size_t)i] : nullptr;
+            cudaEvent_t* ev = c->profiling ? &c->events[6 * (size_t)i] : nullptr;
             if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
-            history_for(c, n, s, ev ? ev[1] : nullptr, ev ? ev[2] : nullptr);
-            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[3], s));
+            history_for(c, n, s, ev ? ev + 1 : nullptr);
+            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[4], s));
             mot::solve_step(c, n, En, c->norms + i, s);
             c->stats.launches += 2;
-            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[4], s));
+            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[5], s));
             if (J_out) {
                 double* dst = J_out + (long long)i * 3 * c->M;
                 if (dev_out) {
@@ -322,13 +366,14 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
         c->stats.cg_iters += hs[3];
         if (c->profiling) {
             for (int i = 0; i < n_steps; ++i) {
-                float t[4];
-                cudaEvent_t* ev = &c->events[5 * (size_t)i];
-                for (int k = 0; k < 4; ++k) MOT_CUDA_TRY(cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
+                float t[5];
+                cudaEvent_t* ev = &c->events[6 * (size_t)i];
+                for (int k = 0; k < 5; ++k) MOT_CUDA_TRY(cudaEventElapsedTime(&t[k], ev[k], ev[k + 1]));
                 c->stats.ms_fft_fwd += t[0];
-                c->stats.ms_mac += t[1];
-                c->stats.ms_fft_inv += t[2];
-                c->stats.ms_solve += t[3];
+                c->stats.ms_far += t[1];
+                c->stats.ms_mac += t[2];
+                c->stats.ms_fft_inv += t[3];
+                c->stats.ms_solve += t[4];
             }
         }
         for (int i = 0; i < n_steps; ++i) {
@@ -396,6 +441,88 @@ mot_status mot_eval_history(mot_ctx* c, int n_hist, const double* J_hist, double
         reset_state(c, s);
         MOT_CUDA_TRY(cudaStreamSynchronize(s));
     });
+}
+
+mot_status mot_adjoint(mot_ctx* c, int n_steps, const double* J, const double* dO_dJ,
+                       double* grad_eps, double* lambda, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_steps < 1 || !J || !dO_dJ || !grad_eps) {
+        c->err = "n_steps >= 1 and J, dO_dJ, grad_eps non-null required";
+        return MOT_ERR_ARG;
+    }
+    mot_status result = MOT_OK;
+    std::vector<void*> owned;
+    mot_status st = guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        const long long step = 3 * c->M;
+        const long long bytes = sizeof(double) * step * n_steps;
+        auto device_copy = [&](const double* src) -> const double* {
+            if (is_device_ptr(src)) return src;
+            double* d = nullptr;
+            MOT_CUDA_TRY(cudaMalloc(&d, bytes));
+            owned.push_back(d);
+            MOT_CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+            return d;
+        };
+        const double* Jd = device_copy(J);
+        const double* gd = device_copy(dO_dJ);
+        double* lamd = nullptr;
+        if (lambda) {
+            if (is_device_ptr(lambda)) {
+                lamd = lambda;
+            } else {
+                MOT_CUDA_TRY(cudaMalloc(&lamd, bytes));
+                owned.push_back(lamd);
+            }
+        }
+        double* gchi = nullptr;
+        MOT_CUDA_TRY(cudaMalloc(&gchi, sizeof(double) * c->M));
+        owned.push_back(gchi);
+        MOT_CUDA_TRY(cudaMemsetAsync(gchi, 0, sizeof(double) * c->M, s));
+        if (n_steps > c->norms_cap) {
+            MOT_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(c->norms);
+            c->norms = nullptr;
+            c->norms_cap = 0;
+            MOT_CUDA_TRY(cudaMalloc(&c->norms, sizeof(double) * n_steps));
+            c->norms_cap = n_steps;
+        }
+        reset_state(c, s);
+        c->adjoint = true;
+        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
+        for (int tau = 1; tau <= n_steps; ++tau) {
+            const int n = n_steps + 1 - tau;
+            history_for(c, tau, s);
+            mot::adjoint_step(c, tau, n, gd + (long long)(n - 1) * step, Jd, gchi,
+                              lamd ? lamd + (long long)(n - 1) * step : nullptr,
+                              c->norms + tau - 1, s);
+        }
+        std::vector<double> g(c->M), e(c->M);
+        int hs[4];
+        MOT_CUDA_TRY(cudaMemcpyAsync(g.data(), gchi, sizeof(double) * c->M, cudaMemcpyDeviceToHost, s));
+        MOT_CUDA_TRY(cudaMemcpyAsync(e.data(), c->eps, sizeof(double) * c->M, cudaMemcpyDeviceToHost, s));
+        MOT_CUDA_TRY(cudaMemcpyAsync(hs, c->dstatus, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+        if (lambda && lamd != lambda)
+            MOT_CUDA_TRY(cudaMemcpyAsync(lambda, lamd, bytes, cudaMemcpyDeviceToHost, s));
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+        for (long long m = 0; m < c->M; ++m) g[m] /= e[m] * e[m];
+        MOT_CUDA_TRY(cudaMemcpy(grad_eps, g.data(), sizeof(double) * c->M,
+                                is_device_ptr(grad_eps) ? cudaMemcpyHostToDevice
+                                                        : cudaMemcpyHostToHost));
+        c->adjoint = false;
+        reset_state(c, s);
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs[1] & 1) {
+            result = MOT_ERR_NOT_CONVERGED;
+            c->err = "adjoint: CG did not converge";
+        } else if (hs[1] & 2) {
+            result = MOT_ERR_UNSTABLE;
+            c->err = "adjoint: NaN or Inf in lambda";
+        }
+    });
+    for (void* p : owned) cudaFree(p);
+    c->adjoint = false;
+    return st != MOT_OK ? st : result;
 }
 
 mot_status mot_get_table(mot_ctx* c, int l0, int n_lags, double* out) {

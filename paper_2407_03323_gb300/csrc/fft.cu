@@ -17,135 +17,18 @@
 
 #include <algorithm>
 
+#include "fft_core.cuh"
+
+using namespace mot_fft;
+
 namespace {
 
 constexpr int NT = 256;
 
-template <typename R> struct Tile { static constexpr int TB = 16; };
-template <> struct Tile<float> { static constexpr int TB = 32; };
-
-// ------------------------------------------------------------------ butterflies
-// dir = -1 forward (exp(-i...)), +1 inverse; W(m) = exp(dir 2 pi i m / P) from table
-template <typename C>
-__device__ __forceinline__ C twid(const C* tw, int m, int dir) {
-    C w = tw[m];
-    if (dir > 0) w.y = -w.y;
-    return w;
-}
-
-template <typename C, int R>
-__device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
-    if constexpr (R == 2) {
-        C a = v[0], b = v[1];
-        v[0] = cadd(a, b);
-        v[1] = csub(a, b);
-    } else if constexpr (R == 4) {
-        C a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-        C b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
-        // -i * dir' : forward multiplies b1 by -i, inverse by +i
-        C jb1;
-        if (dir < 0) { jb1.x = b1.y; jb1.y = -b1.x; } else { jb1.x = -b1.y; jb1.y = b1.x; }
-        v[0] = cadd(a0, b0);
-        v[2] = csub(a0, b0);
-        v[1] = cadd(a1, jb1);
-        v[3] = csub(a1, jb1);
-    } else {
-        // odd radix: out[q] = v0 + sum_r (s_r cos(2 pi q r/R) -/+ i d_r sin(2 pi q r/R))
-        constexpr int H = (R - 1) / 2;
-        C s[H], d[H];
-        C v0 = v[0];
-        C sum = v0;
-#pragma unroll
-        for (int r = 1; r <= H; ++r) {
-            s[r - 1] = cadd(v[r], v[R - r]);
-            d[r - 1] = csub(v[r], v[R - r]);
-            sum = cadd(sum, s[r - 1]);
-        }
-        const int step = P / R;
-#pragma unroll
-        for (int q = 1; q <= H; ++q) {
-            C A = v0, B;
-            B.x = 0; B.y = 0;
-#pragma unroll
-            for (int r = 1; r <= H; ++r) {
-                const C w = tw[((q * r) % R) * step];   // cos - i sin (forward table)
-                const auto cs = w.x, sn = -w.y;
-                A.x += s[r - 1].x * cs;
-                A.y += s[r - 1].y * cs;
-                B.x += d[r - 1].x * sn;
-                B.y += d[r - 1].y * sn;
-            }
-            // forward: out[q] = A - i B, out[R-q] = A + i B ; inverse: swapped
-            C mB;   // -i B
-            mB.x = B.y; mB.y = -B.x;
-            if (dir < 0) {
-                v[q] = cadd(A, mB);
-                v[R - q] = csub(A, mB);
-            } else {
-                v[q] = csub(A, mB);
-                v[R - q] = cadd(A, mB);
-            }
-        }
-        v[0] = sum;
-    }
-}
-
-template <typename C, int R>
-__device__ __forceinline__ void stage(const C* __restrict__ x, C* __restrict__ y, int P, int Ns,
-                                      int TB, int ld, const C* tw, int dir) {
-    const int nb = P / R;
-    const int items = nb * TB;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int t = it % TB, j = it / TB;
-        const int k = j % Ns;
-        C v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = x[(j + r * nb) * ld + t];
-        if (Ns > 1) {
-            const int tstep = P / (Ns * R);
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid(tw, (r * k * tstep) % P, dir));
-        }
-        dft_small<C, R>(v, tw, P, dir);
-        const int base = (j / Ns) * Ns * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) y[(base + r * Ns) * ld + t] = v[r];
-    }
-}
-
-// runs all stages; returns the buffer holding the result
-template <typename C>
-__device__ C* fft_tile(C* b0, C* b1, int P, const int* rad, int nrad, int TB, int ld,
-                       const C* tw, int dir) {
-    int Ns = 1;
-    C* x = b0;
-    C* y = b1;
-    for (int s = 0; s < nrad; ++s) {
-        const int R = rad[s];
-        switch (R) {
-            case 2: stage<C, 2>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 3: stage<C, 3>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 4: stage<C, 4>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 5: stage<C, 5>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 7: stage<C, 7>(x, y, P, Ns, TB, ld, tw, dir); break;
-        }
-        __syncthreads();
-        Ns *= R;
-        C* tmp = x; x = y; y = tmp;
-    }
-    return x;
-}
-
-struct RadixList {
-    int P;
-    int n;
-    int r[16];
-};
-
-template <typename C>
-__device__ __forceinline__ void load_tw(C* stw, const C* tw, int P) {
-    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
-}
+// lines per CTA: 8 (FP64) / 16 (FP32) keeps the shared tile near 60 KB at P = 210,
+// so that several CTAs are resident per SM
+template <typename R> struct Tile { static constexpr int TB = 8; };
+template <> struct Tile<float> { static constexpr int TB = 16; };
 
 // ------------------------------------------------------------------ pass x, forward
 // rows (comp, w, v) of a real [3][W][V][U] array, paired (v, v+1) -> [3][W][V][Hu]
@@ -153,7 +36,7 @@ template <typename R>
 __global__ void __launch_bounds__(NT) k_fwd_x(const double* __restrict__ in, int U, int V, int W,
                                               typename CT<R>::c* __restrict__ out,
                                               const typename CT<R>::c* __restrict__ tw,
-                                              RadixList rl) {
+                                              RadixList rl, const double* __restrict__ scale) {
     typedef typename CT<R>::c C;
     constexpr int TB = Tile<R>::TB;
     constexpr int ld = TB + 1;
@@ -176,8 +59,14 @@ __global__ void __launch_bounds__(NT) k_fwd_x(const double* __restrict__ in, int
             const long long cw = pr / VP;
             const int v = (int)(pr % VP) * 2;
             const double* row = in + (cw * V + v) * (long long)U;
-            z.x = (R)row[j];
-            if (v + 1 < V) z.y = (R)row[U + j];
+            if (scale) {   // per-voxel factor (the adjoint transforms chi * lambda)
+                const long long m0 = ((cw % W) * V + v) * (long long)U + j;
+                z.x = (R)(row[j] * scale[m0]);
+                if (v + 1 < V) z.y = (R)(row[U + j] * scale[m0 + U]);
+            } else {
+                z.x = (R)row[j];
+                if (v + 1 < V) z.y = (R)row[U + j];
+            }
         }
         b0[j * ld + t] = z;
     }
@@ -360,7 +249,8 @@ void fft_free_axis(AxisFFT& a) {
 }
 
 template <typename R>
-void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s) {
+void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s,
+                 const double* scale) {
     typedef typename CT<R>::c C;
     HistoryBuffers<R>& hb = hbuf<R>(c);
     constexpr int TB = Tile<R>::TB;
@@ -373,7 +263,7 @@ void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStr
         set_smem(k_fwd_x<R>, sm);
         k_fwd_x<R><<<(int)((npairs + TB - 1) / TB), NT, sm, s>>>(Jsoa, U, V, W, hb.tmp1,
                                                                  table<R>(c->ax[0]),
-                                                                 radix_list(c->ax[0]));
+                                                                 radix_list(c->ax[0]), scale);
         MOT_LAUNCH_CHECK();
     }
     const int ntile = (Hu + TB - 1) / TB;
@@ -448,8 +338,8 @@ void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s
     }
 }
 
-template void fft_forward<double>(mot_ctx*, const double*, double2*, cudaStream_t);
-template void fft_forward<float>(mot_ctx*, const double*, float2*, cudaStream_t);
+template void fft_forward<double>(mot_ctx*, const double*, double2*, cudaStream_t, const double*);
+template void fft_forward<float>(mot_ctx*, const double*, float2*, cudaStream_t, const double*);
 template void fft_inverse<double>(mot_ctx*, const double2*, double*, cudaStream_t);
 template void fft_inverse<float>(mot_ctx*, const float2*, float*, cudaStream_t);
 

@@ -12,7 +12,26 @@
 // formed with FP32 FMAs and added into the running sum with an error-free two-sum,
 // so the accumulation over up to ell lags adds no error beyond one rounding of the
 // compensated total.
+// Blocked temporal scheme (Secs. 4-5, MOT_HISTORY_BLOCKED): lags 1..B-1 are multiplied
+// every step as above; the lags [S, 2S) for S = B, 2B, 4B, ... form level S.  At every
+// step n0 with (n0 - 1) mod S = 0 the level computes its contribution to the next S
+// histories, y(n0 + j) = sum_{l=S}^{2S-1} Ghat_l Jhat(n0 + j - l), j < S, as one block
+// Toeplitz product by overlap-save: per spectral bin a length-2S FFT over time of the
+// window Jhat(n0 - 2S .. n0 - 1) (read from the ring), a product with the precomputed
+// temporal spectrum of [Ghat_S .. Ghat_{2S-1}, 0 .. 0], an inverse FFT, and the last
+// S outputs added into a ring of future-history accumulators.  Every time is covered
+// by exactly one firing of the largest level, which happens no later than any other
+// firing covering it; that level writes the accumulators and the others add to them.
+// The per-step near MAC adds the accumulator of its step.  A level's inputs are all older than n0,
+// so the scheme is causal (the division of Sec. 4.1 into Toeplitz blocks that use only
+// computed currents); levels double in length so a step costs O(log ell) block work on
+// average, the temporal counterpart of Eq. ComplexityHierarchicalDivisionInTime.
 #include "mot_internal.cuh"
+#include "fft_core.cuh"
+
+#include <algorithm>
+
+using namespace mot_fft;
 
 namespace {
 
@@ -56,7 +75,8 @@ template <typename R>
 __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
                                             const typename CT<R>::c* __restrict__ ring, int hring,
                                             int slot_first, int L, MacGeom g, R scale,
-                                            typename CT<R>::c* __restrict__ phat) {
+                                            typename CT<R>::c* __restrict__ phat,
+                                            typename CT<R>::c* __restrict__ acc) {
     typedef typename CT<R>::c C;
     typedef typename std::conditional<std::is_same<R, double>::value, double2, float2>::type R2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -78,6 +98,11 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
     const R syz = (fv != fw) ? (R)-1 : (R)1;
     Acc<R> ax, ay, az;
     ax.zero(); ay.zero(); az.zero();
+    if (acc) {   // far-lag contributions of this step (the top level rewrites the slot)
+        ax.add(acc[bidx]);
+        ay.add(acc[g.nbins + bidx]);
+        az.add(acc[2 * g.nbins + bidx]);
+    }
     const long long slot_stride = 3 * g.nbins;
     int slot = slot_first;
     const R2* gp = reinterpret_cast<const R2*>(ghat + o * 6);
@@ -109,6 +134,142 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
     v = az.get(); v.x *= scale; v.y *= scale; phat[2 * g.nbins + bidx] = v;
 }
 
+// temporal spectra of level S: H(w) = sum_{m=0}^{lmax-S} Ghat_{S+m} exp(-2 pi i w m / (2S)),
+// w = 0..S (the rest follows by H(2S - w) = conj H(w)); out [w][octant bin][6]
+template <typename R>
+__global__ void k_level_spec(const R* __restrict__ ghat, long long noct, int S, int lmax,
+                             const double2* __restrict__ tw, typename CT<R>::c* __restrict__ out) {
+    typedef typename CT<R>::c C;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= noct * (S + 1)) return;
+    const long long o = i % noct;
+    const int w = (int)(i / noct);
+    double2 acc[6];
+    for (int c = 0; c < 6; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int m = 0; m <= lmax - S; ++m) {
+        const double2 t = tw[((long long)w * m) % (2 * S)];
+        const R* gp = ghat + ((long long)(S + m - 1) * noct + o) * 6;
+        for (int c = 0; c < 6; ++c) {
+            const double g = (double)gp[c];
+            acc[c].x += g * t.x;
+            acc[c].y += g * t.y;
+        }
+    }
+    C* op = out + ((long long)w * noct + o) * 6;
+    for (int c = 0; c < 6; ++c) {
+        C v;
+        v.x = acc[c].x;
+        v.y = acc[c].y;
+        op[c] = v;
+    }
+}
+
+template <typename R> struct FarArgs {
+    typedef typename CT<R>::c C;
+    const C* ring;
+    int hring;
+    long long nbins, noct;
+    const C* H;          // level spectra [S+1][noct][6]
+    C* acc;              // [smax][3][nbins]
+    int smax;
+    int n0, S, lmax;
+    int Hu, Hv, Hw, Pv, Pw;
+    int ntile;
+    int overwrite;       // 1: first writer of these accumulators (top level)
+    RadixList rl;        // length 2S
+    const C* tw;
+};
+
+// one level firing at step n0: adds y(n0 + j), j < S, into the accumulator ring
+template <typename R, int TB>
+__global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
+    typedef typename CT<R>::c C;
+    constexpr int L3 = 3 * TB;
+    constexpr int ld = L3 + 1;
+    const int P = 2 * a.S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* stw = reinterpret_cast<C*>(smem_raw);
+    C* b0 = stw + P;
+    C* b1 = b0 + P * ld;
+    // block -> (octant row, mirror, ku tile); the four mirrors of a row are adjacent
+    const int ut = blockIdx.x % a.ntile;
+    const int rest = blockIdx.x / a.ntile;
+    const int mirror = rest & 3;
+    const int orow = rest >> 2;
+    const int kv_o = orow % a.Hv, kw_o = orow / a.Hv;
+    const bool fv = (mirror & 1) != 0, fw = (mirror & 2) != 0;
+    const bool mv = kv_o > 0 && 2 * kv_o < a.Pv;
+    const bool mw = kw_o > 0 && 2 * kw_o < a.Pw;
+    if ((fv && !mv) || (fw && !mw)) return;
+    const int kv = fv ? a.Pv - kv_o : kv_o;
+    const int kw = fw ? a.Pw - kw_o : kw_o;
+    const int ku0 = ut * TB;
+    const long long row = ((long long)kw * a.Pv + kv) * a.Hu + ku0;
+    const long long orow_base = ((long long)kw_o * a.Hv + kv_o) * a.Hu + ku0;
+    const R sxy = fv ? (R)-1 : (R)1;
+    const R sxz = fw ? (R)-1 : (R)1;
+    const R syz = (fv != fw) ? (R)-1 : (R)1;
+    load_tw(stw, a.tw, P);
+    const int tfirst = max(1, a.n0 - a.lmax);
+    for (int it = threadIdx.x; it < P * L3; it += blockDim.x) {
+        const int i = it / L3, t = it % L3;
+        const int comp = t / TB, bb = t % TB;
+        const int time = a.n0 - P + i;
+        C v;
+        v.x = 0; v.y = 0;
+        if (time >= tfirst && ku0 + bb < a.Hu) {
+            const long long slot = time % a.hring;
+            v = a.ring[(slot * 3 + comp) * a.nbins + row + bb];
+        }
+        b0[i * ld + t] = v;
+    }
+    __syncthreads();
+    C* X = fft_tile(b0, b1, P, a.rl.r, a.rl.n, L3, ld, stw, -1);
+    C* other = (X == b0) ? b1 : b0;
+    for (int it = threadIdx.x; it < P * TB; it += blockDim.x) {
+        const int w = it / TB, bb = it % TB;
+        if (ku0 + bb >= a.Hu) continue;
+        const bool cj = w > a.S;
+        const int ws = cj ? P - w : w;
+        const C* hp = a.H + ((long long)ws * a.noct + orow_base + bb) * 6;
+        C h[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            h[c] = hp[c];
+            if (cj) h[c].y = -h[c].y;
+        }
+        h[3].x *= sxy; h[3].y *= sxy;
+        h[4].x *= sxz; h[4].y *= sxz;
+        h[5].x *= syz; h[5].y *= syz;
+        C* xp = X + w * ld + bb;
+        const C x0 = xp[0], x1 = xp[TB], x2 = xp[2 * TB];
+        xp[0] = cadd(cadd(cmul(h[0], x0), cmul(h[3], x1)), cmul(h[4], x2));
+        xp[TB] = cadd(cadd(cmul(h[3], x0), cmul(h[1], x1)), cmul(h[5], x2));
+        xp[2 * TB] = cadd(cadd(cmul(h[4], x0), cmul(h[5], x1)), cmul(h[2], x2));
+    }
+    __syncthreads();
+    C* Y = fft_tile(X, other, P, a.rl.r, a.rl.n, L3, ld, stw, +1);
+    const R scale = (R)1 / (R)P;
+    for (int it = threadIdx.x; it < a.S * L3; it += blockDim.x) {
+        const int j = it / L3, t = it % L3;
+        const int comp = t / TB, bb = t % TB;
+        if (ku0 + bb >= a.Hu) continue;
+        const long long slot = (long long)((a.n0 + j) % a.smax);
+        C* dst = a.acc + (slot * 3 + comp) * a.nbins + row + bb;
+        const C y = Y[(a.S + j) * ld + t];
+        C v;
+        if (a.overwrite) {
+            v.x = y.x * scale;
+            v.y = y.y * scale;
+        } else {
+            v = *dst;
+            v.x += y.x * scale;
+            v.y += y.y * scale;
+        }
+        *dst = v;
+    }
+}
+
 MacGeom geom(const mot_ctx* c) {
     MacGeom g;
     g.Hu = c->Hu; g.Hv = c->Hv; g.Hw = c->Hw;
@@ -133,6 +294,22 @@ void history_alloc(mot_ctx* c) {
     MOT_CUDA_TRY(cudaMalloc(&hb.tmp1, sizeof(C) * 3LL * c->W * c->V * c->Hu));
     MOT_CUDA_TRY(cudaMalloc(&hb.tmp2, sizeof(C) * 3LL * c->W * c->ax[1].P * c->Hu));
     MOT_CUDA_TRY(cudaMalloc(&hb.hist_spatial, sizeof(R) * 3 * c->M));
+    if (c->scheme == MOT_HISTORY_BLOCKED) {
+        c->nlev = 0;
+        long long spec = 0;
+        for (int S = c->block; S <= c->ell && c->nlev < 8; S *= 2) {
+            c->lev_S[c->nlev] = S;
+            c->lev_off[c->nlev] = spec;
+            spec += (long long)(S + 1) * c->noct * 6;
+            fft_plan_axis(c->lev_fft[c->nlev], 2 * S);
+            ++c->nlev;
+        }
+        c->smax = c->nlev ? c->lev_S[c->nlev - 1] : 1;
+        if (c->nlev && 2 * c->lev_S[c->nlev - 1] < c->ell + 1)
+            throw MotError{MOT_ERR_ARG, "blocked scheme: more than 8 levels needed; raise block"};
+        MOT_CUDA_TRY(cudaMalloc(&hb.level_spec, sizeof(C) * std::max<long long>(spec, 1)));
+        MOT_CUDA_TRY(cudaMalloc(&hb.acc_ring, sizeof(C) * slot * c->smax));
+    }
 }
 
 template <typename R>
@@ -154,28 +331,105 @@ void history_reset(mot_ctx* c, cudaStream_t s) {
     typedef typename CT<R>::c C;
     HistoryBuffers<R>& hb = hbuf<R>(c);
     MOT_CUDA_TRY(cudaMemsetAsync(hb.jhat_ring, 0, sizeof(C) * 3 * c->nbins * c->hring, s));
+    if (hb.acc_ring)
+        MOT_CUDA_TRY(cudaMemsetAsync(hb.acc_ring, 0, sizeof(C) * 3 * c->nbins * c->smax, s));
+}
+
+// temporal spectra of every level from the spatial spectra (setup)
+template <typename R>
+void level_spectra(mot_ctx* c) {
+    HistoryBuffers<R>& hb = hbuf<R>(c);
+    for (int k = 0; k < c->nlev; ++k) {
+        const int S = c->lev_S[k];
+        const int lmax = std::min(2 * S - 1, c->ell);
+        const long long n = c->noct * (S + 1);
+        k_level_spec<R><<<(int)((n + NT - 1) / NT), NT, 0, c->stream>>>(
+            hb.ghat, c->noct, S, lmax, c->lev_fft[k].tw64, hb.level_spec + c->lev_off[k]);
+        MOT_LAUNCH_CHECK();
+    }
+    MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+}
+
+template <typename R> const typename CT<R>::c* twtab(const AxisFFT& a);
+template <> const double2* twtab<double>(const AxisFFT& a) { return a.tw64; }
+template <> const float2* twtab<float>(const AxisFFT& a) { return a.tw32; }
+
+template <typename R, int TB>
+void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
+    typedef typename CT<R>::c C;
+    a.ntile = (c->Hu + TB - 1) / TB;
+    const int P = 2 * a.S;
+    const size_t sm = sizeof(C) * ((size_t)P + 2 * (size_t)P * (3 * TB + 1));
+    if (sm > 227 * 1024) throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
+    k_far<R, TB><<<(int)blocks, NT, sm, s>>>(a);
+    MOT_LAUNCH_CHECK();
+}
+
+template <typename R>
+void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
+    HistoryBuffers<R>& hb = hbuf<R>(c);
+    FarArgs<R> a;
+    a.ring = hb.jhat_ring;
+    a.hring = c->hring;
+    a.nbins = c->nbins;
+    a.noct = c->noct;
+    a.H = hb.level_spec + c->lev_off[k];
+    a.acc = hb.acc_ring;
+    a.smax = c->smax;
+    a.n0 = n0;
+    a.S = c->lev_S[k];
+    a.lmax = std::min(2 * a.S - 1, c->ell);
+    a.Hu = c->Hu; a.Hv = c->Hv; a.Hw = c->Hw;
+    a.Pv = c->ax[1].P; a.Pw = c->ax[2].P;
+    a.overwrite = (k == c->nlev - 1) ? 1 : 0;
+    const AxisFFT& f = c->lev_fft[k];
+    a.rl.P = f.P;
+    a.rl.n = f.nrad;
+    for (int i = 0; i < 16; ++i) a.rl.r[i] = f.rad[i];
+    a.tw = twtab<R>(f);
+    // lines per CTA: 3 components x TB bins; fewer bins for long levels keeps several
+    // CTAs resident per SM
+    const bool fp32 = std::is_same<R, float>::value;
+    if (a.S <= 32) {
+        if (fp32) far_launch<R, 8>(c, a, s); else far_launch<R, 4>(c, a, s);
+    } else {
+        if (fp32) far_launch<R, 4>(c, a, s); else far_launch<R, 2>(c, a, s);
+    }
+    c->stats.launches += 1;
+    c->stats.far_launches += 1;
 }
 
 // hist_spatial <- sum_{l=1}^{ell} G_l * J_{n-l}; J_{n-1} is read from the spatial ring
 template <typename R>
-void history_step(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t ev_fwd, cudaEvent_t ev_mac) {
+void history_step(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t* ev) {
+    typedef typename CT<R>::c C;
     HistoryBuffers<R>& hb = hbuf<R>(c);
     const long long slot = 3 * c->nbins;
     if (n >= 2) {
         const double* Jprev = c->J + slot_index(n - 1, c->jring) * 3 * c->M;
-        fft_forward<R>(c, Jprev, hb.jhat_ring + slot_index(n - 1, c->hring) * slot, s);
+        fft_forward<R>(c, Jprev, hb.jhat_ring + slot_index(n - 1, c->hring) * slot, s,
+                       c->adjoint ? c->chi : nullptr);
         c->stats.launches += 3;
     }
-    if (ev_fwd) MOT_CUDA_TRY(cudaEventRecord(ev_fwd, s));
+    if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
+    const bool blocked = c->scheme == MOT_HISTORY_BLOCKED;
+    if (blocked)   // largest level first: it writes the accumulators, the others add
+        for (int k = c->nlev - 1; k >= 0; --k)
+            if ((n - 1) % c->lev_S[k] == 0) far_level<R>(c, k, n, s);
+    if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[1], s));
     const R scale = (R)(1.0 / ((double)c->ax[0].P * c->ax[1].P * c->ax[2].P));
     const long long nblk = (c->noct + 8 * (NT / 32) - 1) / (8 * (NT / 32));
+    const int L = blocked ? std::min(c->block - 1, c->ell) : c->ell;
+    C* acc = blocked ? hb.acc_ring + slot_index(n, c->smax) * slot : nullptr;
     k_mac<R><<<(int)nblk, NT, 0, s>>>(hb.ghat, hb.jhat_ring, c->hring,
-                                      (int)slot_index(n - 1, c->hring), c->ell, geom(c), scale,
-                                      hb.phat);
+                                      (int)slot_index(n - 1, c->hring), L, geom(c), scale,
+                                      hb.phat, acc);
     MOT_LAUNCH_CHECK();
     c->stats.launches += 1;
     c->stats.mac_launches += 1;
-    if (ev_mac) MOT_CUDA_TRY(cudaEventRecord(ev_mac, s));
+    if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[2], s));
     fft_inverse<R>(c, hb.phat, hb.hist_spatial, s);
     c->stats.launches += 3;
 }
@@ -186,7 +440,9 @@ template void history_free<double>(mot_ctx*);
 template void history_free<float>(mot_ctx*);
 template void history_reset<double>(mot_ctx*, cudaStream_t);
 template void history_reset<float>(mot_ctx*, cudaStream_t);
-template void history_step<double>(mot_ctx*, int, cudaStream_t, cudaEvent_t, cudaEvent_t);
-template void history_step<float>(mot_ctx*, int, cudaStream_t, cudaEvent_t, cudaEvent_t);
+template void level_spectra<double>(mot_ctx*);
+template void level_spectra<float>(mot_ctx*);
+template void history_step<double>(mot_ctx*, int, cudaStream_t, cudaEvent_t*);
+template void history_step<float>(mot_ctx*, int, cudaStream_t, cudaEvent_t*);
 
 }  // namespace mot

@@ -97,9 +97,17 @@ struct mot_ctx {
     double* cg_r = nullptr;
     double* cg_p = nullptr;
     double* cg_q = nullptr;
-    float* cg32 = nullptr;       // FP32 inner CG vectors r, p, q, e ([4][3][M])
+    float* cg32 = nullptr;       // FP32 inner CG vectors r, p, q, e ([4][M] float4)
     int* active = nullptr;       // voxels with chi > 0
+    int* nmask = nullptr;        // per active voxel: in-grid neighbours (27 bits)
+    float* diag32 = nullptr;     // FP32 copy of cg_diag
+    double* vfac = nullptr;      // [4][M]: 0.5/eps, 1/chi (0 if chi = 0), 1/(0.5/eps + d0), chi
     long long nact = 0;
+    double cheb_lmin = 0.0, cheb_lmax = 0.0;   // spectral bounds of diag(1/chi) Z_0
+    int cheb_n = 0;
+    double cheb_log_rate = -1.0;
+    float cheb_inv_theta = 0.f;
+    float cheb_c1[64] = {0}, cheb_c2[64] = {0};
     double* red = nullptr;       // reduction scratch
     int* dstatus = nullptr;      // [0] cg iterations of last step, [1] flags
     double* norms = nullptr;     // per-step ||J_n||^2 of the current call
@@ -121,13 +129,18 @@ struct mot_ctx {
 
     HistoryBuffers<double> h64;
     HistoryBuffers<float> h32;
-    int nlev = 0;                // blocked scheme levels
+    int nlev = 0;                // blocked scheme levels S = B, 2B, ...
     int lev_S[8] = {0};
+    long long lev_off[8] = {0};  // offsets of the level spectra
+    AxisFFT lev_fft[8];          // temporal FFT plans of length 2S
+    int smax = 1;                // accumulator ring length (largest S)
+
+    bool adjoint = false;        // rings hold lambda; the FFT input is chi * lambda
 
     // counters and optional phase timing
     mot_stats stats = {};
     bool profiling = false;
-    std::vector<cudaEvent_t> events;   // 5 per step of the current call
+    std::vector<cudaEvent_t> events;   // 6 per step of the current call
 
     cudaStream_t stream = nullptr;
     int nsm = 0;
@@ -154,22 +167,28 @@ void spectrum_of_lag(mot_ctx* c, int l, double* host_out);
 void fft_plan_axis(AxisFFT& a, int P);
 void fft_free_axis(AxisFFT& a);
 template <typename R>
-void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s);
+void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s,
+                 const double* scale = nullptr);
 template <typename R>
 void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s);
 // history.cu
 template <typename R> void history_alloc(mot_ctx* c);
 template <typename R> void history_free(mot_ctx* c);
-// ev (optional): events recorded after the forward FFT and after the MAC
+// ev (optional, 3 events): recorded after the forward FFT, after the far-lag block
+// products and after the near-lag MAC
 template <typename R> void history_step(mot_ctx* c, int n, cudaStream_t s,
-                                        cudaEvent_t ev_fwd = nullptr, cudaEvent_t ev_mac = nullptr);
+                                        cudaEvent_t* ev = nullptr);
 template <typename R> void history_reset(mot_ctx* c, cudaStream_t s);
+template <typename R> void level_spectra(mot_ctx* c);
 // solve.cu
 void solve_step(mot_ctx* c, int n, const double* En, double* norm2_out, cudaStream_t s);
 void stencil_setup(mot_ctx* c);
+void chebyshev_setup(mot_ctx* c);
 void write_aos(mot_ctx* c, int n, double* out_dev, cudaStream_t s);
 void read_aos(mot_ctx* c, const double* in_dev, double* slot, cudaStream_t s);
 void history_out(mot_ctx* c, int n, double* out_dev, cudaStream_t s);
+void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double* J_aos,
+                  double* grad_chi, double* lam_out, double* norm2_out, cudaStream_t s);
 // excitation.cu
 void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, double st,
                 double t0, int n_first, int n_steps, double* Edev, cudaStream_t s);

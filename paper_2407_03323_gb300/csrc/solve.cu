@@ -15,12 +15,16 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
+#include <cmath>
+
 namespace cg = cooperative_groups;
 
 namespace {
 
 constexpr int NT = 256;
 constexpr int MAXTAPS = 64;
+constexpr int MAXCHEB = 64;
 
 __constant__ double c_stencil[27 * 6];   // G_0(e) for e in {-1,0,1}^3, order xx yy zz xy xz yz
 __constant__ double c_taps[MAXTAPS];
@@ -32,9 +36,11 @@ __device__ __forceinline__ long long jslot(int s0, int l, int jring, long long s
     return (long long)sl * stride;
 }
 
+// per-voxel factors precomputed at setup (no FP64 divisions in the step):
+//   f[0][m] = T(1)/eps_m = 0.5/eps_m, f[1][m] = 1/chi_m (0 if chi_m = 0),
+//   f[2][m] = 1/(T(0)/eps_m + delta_0) (used where chi_m = 0), f[3][m] = chi_m
 template <typename R>
-__global__ void k_epilogue(long long M, const double* __restrict__ eps,
-                           const double* __restrict__ chi, const double* __restrict__ En,
+__global__ void k_epilogue(long long M, const double* __restrict__ f, const double* __restrict__ En,
                            const R* __restrict__ hist, double* __restrict__ Jring, int s0,
                            int jring, int n_taps, double* __restrict__ b) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -43,90 +49,109 @@ __global__ void k_epilogue(long long M, const double* __restrict__ eps,
     const int beta = (int)(i / M);
     const long long st = 3 * M;
     const double e = En ? En[m * 3 + beta] : 0.0;
-    const double ep = eps[m], ch = chi[m];
     const double j1 = Jring[jslot(s0, 1, jring, st) + i];
     const double j2 = Jring[jslot(s0, 2, jring, st) + i];
     const double j3 = Jring[jslot(s0, 3, jring, st) + i];
-    double P = 0.5 / ep * j1 - ch * (double)hist[i];
+    double P = f[m] * j1 - f[3 * M + m] * (double)hist[i];
     for (int l = 1; l < n_taps; ++l) P += c_taps[l] * Jring[jslot(s0, l, jring, st) + i];
     const double rhs = e - P;
     double* Jn = Jring + jslot(s0, 0, jring, st);
-    if (ch > 0.0) {
-        b[i] = rhs / ch;
+    const double ichi = f[M + m];
+    if (ichi > 0.0) {
+        b[i] = rhs * ichi;
         Jn[i] = 3.0 * j1 - 3.0 * j2 + j3;      // quadratic extrapolation as CG start
     } else {
         b[i] = 0.0;
-        Jn[i] = rhs / (0.5 / ep + (n_taps > 0 ? c_taps[0] : 0.0));
+        Jn[i] = rhs * f[2 * M + m];
     }
 }
 
 struct CGArgs {
     long long M;
-    int U, V, W;
     const int* act;       // active voxels (chi > 0)
+    const int* nmask;     // per active voxel: bit e set if neighbour e (0..26) is in the grid
     long long nact;
-    double* x;            // J_n slot (in/out)
-    const double* b;
-    double* r64;          // FP64 residual
-    float* r;             // FP32 inner vectors
-    float* p;
-    float* q;
-    float* e;
+    double* x;            // J_n slot (in/out), SoA [3][M]
+    const double* b;      // rhs / chi, SoA
+    const float* diag32;  // A's diagonal (T(0)/eps + delta_0)/chi, FP32 copy
     const double* diag;
+    double* r64;          // FP64 residual, SoA
+    float4* r;            // FP32 inner vectors, one float4 (x, y, z, 0) per voxel
+    float4* p;
+    float4* q;
+    float4* e;
     double* red;          // [3][gridDim]
     double tol2;          // outer tolerance^2 (relative to ||b||^2)
-    float tin2;           // inner tolerance^2 (relative to the scaled residual)
-    int max_inner;        // inner iterations per refinement
+    float inv_theta;      // Chebyshev: 1 / theta, theta = (lmin + lmax) / 2
+    int n_cheb;           // most Chebyshev iterations per refinement (<= MAXCHEB)
+    double log_rate;      // log of the Chebyshev convergence rate (< 0)
+    float c1[MAXCHEB];    // d_{k+1} = c1[k] d_k + c2[k] r_{k+1}
+    float c2[MAXCHEB];
     int max_iter;         // cap on total inner iterations
     int max_outer;
     int step;             // time index n (for the status record)
-    int* status;          // [0] inner its, [1] flags, [2] first bad step, [3] total its, 
+    int* status;          // [0] inner its, [1] flags, [2] first bad step, [3] total its
     double* norm2;        // ||x||^2 output
 };
 
-// the 13 offsets e > 0 (lexicographic in (ez, ey, ex)); G_0(-e) = G_0(e)
-__constant__ int c_pair[13][3] = {{1, 0, 0},  {-1, 1, 0}, {0, 1, 0},  {1, 1, 0},  {-1, -1, 1},
-                                  {0, -1, 1}, {1, -1, 1}, {-1, 0, 1}, {0, 0, 1},  {1, 0, 1},
-                                  {-1, 1, 1}, {0, 1, 1},  {1, 1, 1}};
+// neighbour e = (ez+1)*9 + (ey+1)*3 + (ex+1); c_noff[e] = ex + U ey + U V ez
+__constant__ int c_noff[27];
+__constant__ float c_st32[27 * 6];   // FP32 copy of c_stencil
+// the 13 neighbours e > 13 (the mirror of e is 26 - e); G_0(-e) = G_0(e)
+constexpr int kPairs = 13;
 
-// (A x)_m = diag_m x_m - sum_e G_0(e) x_{m+e} for an active voxel m, written as
-// center + 13 symmetric pairs: G_0(e) (x_{m+e} + x_{m-e}).  x is zero off the active set.
-template <typename T>
-__device__ __forceinline__ void applyA(const CGArgs& a, const T* __restrict__ x, long long m,
-                                       T o[3]) {
+// (A x)_m in FP64 for an active voxel: centre + 13 symmetric pairs
+__device__ __forceinline__ void applyA64(const CGArgs& a, const double* __restrict__ x, int m,
+                                         int mask, double o[3]) {
     const long long M = a.M;
-    const int u = (int)(m % a.U), v = (int)((m / a.U) % a.V), w = (int)(m / ((long long)a.U * a.V));
-    const double* S0 = c_stencil + 13 * 6;   // e = 0
-    const T X0 = x[m], Y0 = x[M + m], Z0 = x[2 * M + m];
-    const T d = (T)a.diag[m];
-    T o0 = (d - (T)S0[0]) * X0, o1 = (d - (T)S0[1]) * Y0, o2 = (d - (T)S0[2]) * Z0;
-#pragma unroll
-    for (int k = 0; k < 13; ++k) {
-        const int ex = c_pair[k][0], ey = c_pair[k][1], ez = c_pair[k][2];
-        T sx = 0, sy = 0, sz = 0;
-        {
-            const int u2 = u + ex, v2 = v + ey, w2 = w + ez;
-            if (u2 >= 0 && u2 < a.U && v2 >= 0 && v2 < a.V && w2 >= 0 && w2 < a.W) {
-                const long long m2 = ((long long)w2 * a.V + v2) * a.U + u2;
-                sx += x[m2]; sy += x[M + m2]; sz += x[2 * M + m2];
-            }
+    const double* S0 = c_stencil + 13 * 6;
+    const double d = a.diag[m];
+    double o0 = (d - S0[0]) * x[m], o1 = (d - S0[1]) * x[M + m], o2 = (d - S0[2]) * x[2 * M + m];
+#pragma unroll 1
+    for (int k = 0; k < kPairs; ++k) {
+        const int ep = 14 + k, em = 12 - k;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        if (mask & (1 << ep)) {
+            const int m2 = m + c_noff[ep];
+            sx += x[m2]; sy += x[M + m2]; sz += x[2 * M + m2];
         }
-        {
-            const int u2 = u - ex, v2 = v - ey, w2 = w - ez;
-            if (u2 >= 0 && u2 < a.U && v2 >= 0 && v2 < a.V && w2 >= 0 && w2 < a.W) {
-                const long long m2 = ((long long)w2 * a.V + v2) * a.U + u2;
-                sx += x[m2]; sy += x[M + m2]; sz += x[2 * M + m2];
-            }
+        if (mask & (1 << em)) {
+            const int m2 = m + c_noff[em];
+            sx += x[m2]; sy += x[M + m2]; sz += x[2 * M + m2];
         }
-        const double* S = c_stencil + ((ez + 1) * 9 + (ey + 1) * 3 + (ex + 1)) * 6;
-        o0 -= (T)S[0] * sx;
-        o1 -= (T)S[1] * sy;
-        o2 -= (T)S[2] * sz;
-        if (ex != 0 && ey != 0) { o0 -= (T)S[3] * sy; o1 -= (T)S[3] * sx; }
-        if (ex != 0 && ez != 0) { o0 -= (T)S[4] * sz; o2 -= (T)S[4] * sx; }
-        if (ey != 0 && ez != 0) { o1 -= (T)S[5] * sz; o2 -= (T)S[5] * sy; }
+        const double* S = c_stencil + ep * 6;
+        o0 -= S[0] * sx + S[3] * sy + S[4] * sz;
+        o1 -= S[3] * sx + S[1] * sy + S[5] * sz;
+        o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
     }
     o[0] = o0; o[1] = o1; o[2] = o2;
+}
+
+// (A x)_m in FP32 on float4 vectors
+__device__ __forceinline__ float4 applyA32(const CGArgs& a, const float4* __restrict__ x, int m,
+                                           int mask) {
+    const float* S0 = c_st32 + 13 * 6;
+    const float d = a.diag32[m];
+    const float4 c = x[m];
+    float o0 = (d - S0[0]) * c.x, o1 = (d - S0[1]) * c.y, o2 = (d - S0[2]) * c.z;
+#pragma unroll
+    for (int k = 0; k < kPairs; ++k) {
+        const int ep = 14 + k, em = 12 - k;
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        if (mask & (1 << ep)) {
+            const float4 v = x[m + c_noff[ep]];
+            sx += v.x; sy += v.y; sz += v.z;
+        }
+        if (mask & (1 << em)) {
+            const float4 v = x[m + c_noff[em]];
+            sx += v.x; sy += v.y; sz += v.z;
+        }
+        const float* S = c_st32 + ep * 6;
+        o0 -= S[0] * sx + S[3] * sy + S[4] * sz;
+        o1 -= S[3] * sx + S[1] * sy + S[5] * sz;
+        o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
+    }
+    return make_float4(o0, o1, o2, 0.f);
 }
 
 // block-wide sum of two values; result valid in every thread
@@ -168,10 +193,10 @@ __device__ __forceinline__ double grid_total(const double* red, int nb) {
 }
 
 // Mixed-precision iterative refinement: FP64 residual r = b - A x, FP32 conjugate
-// gradients for A e = r / ||r|| to a relative 1e-5 or so, x += ||r|| e; repeat until the
+// gradients for A e = r / ||r|| to a relative ~1e-5, x += ||r|| e; repeat until the
 // FP64 residual meets tol ||b||.  All blocks take identical decisions because every
 // block sums the same per-block partials in the same order.
-__global__ void __launch_bounds__(NT) k_cg(CGArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
     cg::grid_group grid = cg::this_grid();
     const long long M = a.M;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -187,17 +212,16 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs a) {
         // ---- FP64 residual
         double rr_p = 0.0, bb_p = 0.0;
         for (long long i = t0; i < a.nact; i += gs) {
-            const long long m = a.act[i];
+            const int m = a.act[i];
             double o[3];
-            applyA<double>(a, a.x, m, o);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double bv = a.b[c * M + m];
-                const double rv = bv - o[c];
-                a.r64[c * M + m] = rv;
-                rr_p += rv * rv;
-                if (first) bb_p += bv * bv;
-            }
+            applyA64(a, a.x, m, a.nmask[i], o);
+            const double b0 = a.b[m], b1 = a.b[M + m], b2 = a.b[2 * M + m];
+            const double r0 = b0 - o[0], r1 = b1 - o[1], r2 = b2 - o[2];
+            rr_p += r0 * r0 + r1 * r1 + r2 * r2;
+            if (first) bb_p += b0 * b0 + b1 * b1 + b2 * b2;
+            a.r64[m] = r0;
+            a.r64[M + m] = r1;
+            a.r64[2 * M + m] = r2;
         }
         block_sum2(rr_p, bb_p);
         if (threadIdx.x == 0) { red0[blockIdx.x] = rr_p; red1[blockIdx.x] = bb_p; }
@@ -208,8 +232,8 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs a) {
         grid.sync();   // all blocks have read red0/red1
         if (bb == 0.0) {
             for (long long i = t0; i < a.nact; i += gs) {
-                const long long m = a.act[i];
-                for (int c = 0; c < 3; ++c) a.x[c * M + m] = 0.0;
+                const int m = a.act[i];
+                a.x[m] = 0.0; a.x[M + m] = 0.0; a.x[2 * M + m] = 0.0;
             }
             rr = 0.0;
             converged = true;
@@ -217,75 +241,52 @@ __global__ void __launch_bounds__(NT) k_cg(CGArgs a) {
         }
         if (rr <= a.tol2 * bb) { converged = true; break; }
         if (!(rr == rr) || outer >= a.max_outer || its >= a.max_iter) break;
-        // ---- FP32 inner CG on the scaled residual
+        // ---- FP32 Chebyshev iteration for A e = r / ||r|| (r holds the FP32 residual).
+        // One fused pass per iteration (apply to d_k, update e, r, d_{k+1}) and one grid
+        // barrier; d is double-buffered because neighbours read d_k during the pass.
+        // iterations for the reduction still needed (with a factor 10 of margin), never
+        // asking for more than FP32 can deliver in one refinement (5e-6)
+        const double need = fmax(0.1 * sqrt(a.tol2 * bb / rr), 5e-6);
+        const int n_it = min(a.n_cheb, max(3, (int)ceil(log(0.5 * need) / a.log_rate)));
+        // normalise in FP64 first: a tiny residual must not underflow in FP32
         const double sc = 1.0 / sqrt(rr);
         for (long long i = t0; i < a.nact; i += gs) {
-            const long long m = a.act[i];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const long long k = c * M + m;
-                const float rv = (float)(a.r64[k] * sc);
-                a.r[k] = rv;
-                a.p[k] = rv;
-                a.e[k] = 0.f;
-            }
+            const int m = a.act[i];
+            const float4 rv = make_float4((float)(a.r64[m] * sc), (float)(a.r64[M + m] * sc),
+                                          (float)(a.r64[2 * M + m] * sc), 0.f);
+            a.r[m] = rv;
+            a.p[m] = make_float4(rv.x * a.inv_theta, rv.y * a.inv_theta, rv.z * a.inv_theta, 0.f);
+            a.e[m] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        double rho = 1.0;          // ||r32||^2 (scaled residual has unit norm)
-        const double stop = (double)a.tin2;
         grid.sync();
-        int k_in = 0;
-        while (rho > stop && k_in < a.max_inner) {
-            double pq = 0.0, dummy = 0.0;
+        float4* dk = a.p;
+        float4* dn = a.q;
+        for (int k = 0; k < n_it; ++k) {
+            const float c1 = a.c1[k], c2 = a.c2[k];
             for (long long i = t0; i < a.nact; i += gs) {
-                const long long m = a.act[i];
-                float o[3];
-                applyA<float>(a, a.p, m, o);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    a.q[c * M + m] = o[c];
-                    pq += (double)a.p[c * M + m] * (double)o[c];
-                }
-            }
-            block_sum2(pq, dummy);
-            if (threadIdx.x == 0) red2[blockIdx.x] = pq;
-            grid.sync();
-            const float alpha = (float)(rho / grid_total(red2, nb));
-            double rn = 0.0;
-            for (long long i = t0; i < a.nact; i += gs) {
-                const long long m = a.act[i];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const long long k = c * M + m;
-                    a.e[k] += alpha * a.p[k];
-                    const float rv = a.r[k] - alpha * a.q[k];
-                    a.r[k] = rv;
-                    rn += (double)rv * (double)rv;
-                }
-            }
-            block_sum2(rn, dummy);
-            if (threadIdx.x == 0) red0[blockIdx.x] = rn;
-            grid.sync();
-            const double rho_new = grid_total(red0, nb);
-            const float beta = (float)(rho_new / rho);
-            rho = rho_new;
-            for (long long i = t0; i < a.nact; i += gs) {
-                const long long m = a.act[i];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const long long k = c * M + m;
-                    a.p[k] = a.r[k] + beta * a.p[k];
-                }
+                const int m = a.act[i];
+                const float4 q = applyA32(a, dk, m, a.nmask[i]);
+                const float4 d = dk[m];
+                float4 ev = a.e[m], rv = a.r[m];
+                ev.x += d.x; ev.y += d.y; ev.z += d.z;
+                rv.x -= q.x; rv.y -= q.y; rv.z -= q.z;
+                a.e[m] = ev;
+                a.r[m] = rv;
+                dn[m] = make_float4(c1 * d.x + c2 * rv.x, c1 * d.y + c2 * rv.y,
+                                    c1 * d.z + c2 * rv.z, 0.f);
             }
             grid.sync();
-            ++k_in;
+            float4* t = dk; dk = dn; dn = t;
         }
-        its += k_in;
+        its += n_it;
         // ---- FP64 correction
         const double back = sqrt(rr);
         for (long long i = t0; i < a.nact; i += gs) {
-            const long long m = a.act[i];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) a.x[c * M + m] += back * (double)a.e[c * M + m];
+            const int m = a.act[i];
+            const float4 ev = a.e[m];
+            a.x[m] += back * (double)ev.x;
+            a.x[M + m] += back * (double)ev.y;
+            a.x[2 * M + m] += back * (double)ev.z;
         }
         grid.sync();
         ++outer;
@@ -329,6 +330,67 @@ __global__ void k_from_aos(const double* __restrict__ in, long long M, double* _
     x[c * M + m] = in[i];
 }
 
+// ---------------------------------------------------------------- adjoint march
+// In adjoint time tau = N + 1 - n the ring holds lambda.  With mu = chi lambda,
+//   Z_0^T lambda_n = g_n - sum_{l>=1} Z_l^T lambda_{n+l},
+//   Z_l^T lambda = (T(l)/eps + delta_l) lambda - G_l * (chi lambda)      (G_l^T = G_l),
+// and Z_0^T lambda = A mu with the same symmetric A as the forward solve.
+template <typename R>
+__global__ void k_epilogue_adj(long long M, const double* __restrict__ f,
+                               const double* __restrict__ g, const R* __restrict__ hist,
+                               double* __restrict__ Lring, int s0, int jring, int n_taps,
+                               double* __restrict__ b) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * M) return;
+    const long long m = i % M;
+    const int beta = (int)(i / M);
+    const long long st = 3 * M;
+    const double l1 = Lring[jslot(s0, 1, jring, st) + i];
+    const double l2 = Lring[jslot(s0, 2, jring, st) + i];
+    const double l3 = Lring[jslot(s0, 3, jring, st) + i];
+    double P = f[m] * l1 - (double)hist[i];
+    for (int l = 1; l < n_taps; ++l) P += c_taps[l] * Lring[jslot(s0, l, jring, st) + i];
+    const double rhs = g[m * 3 + beta] - P;
+    double* Ln = Lring + jslot(s0, 0, jring, st);
+    const double chi = f[3 * M + m];
+    if (chi > 0.0) {
+        b[i] = rhs;                                    // A mu = rhs
+        Ln[i] = chi * (3.0 * l1 - 3.0 * l2 + l3);      // start: chi times extrapolated lambda
+    } else {
+        b[i] = 0.0;
+        Ln[i] = rhs * f[2 * M + m];
+    }
+}
+
+// lambda = mu / chi on active voxels, gradient accumulation
+//   dO/dchi_m += lambda_n,m . (1/chi_m) sum_l (T(l) + delta_l) J_{n-l,m}
+// (the chi-derivative of row m of the forward system, simplified with that row's own
+// equation), and optional AoS output of lambda_n
+__global__ void k_adj_post(long long M, const double* __restrict__ f, double* __restrict__ Ln,
+                           const double* __restrict__ J, int n, int n_taps,
+                           double* __restrict__ grad_chi, double* __restrict__ lam_out) {
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const double ichi = f[M + m];
+    double gsum = 0.0;
+    for (int beta = 0; beta < 3; ++beta) {
+        double lam = Ln[beta * M + m];
+        if (ichi > 0.0) {
+            lam *= ichi;
+            Ln[beta * M + m] = lam;
+            double q = 0.0;
+            const int L = n_taps > 2 ? n_taps : 2;
+            for (int l = 0; l < L && n - l >= 1; ++l) {
+                const double w = (l < 2 ? 0.5 : 0.0) + (l < n_taps ? c_taps[l] : 0.0);
+                q += w * J[((long long)(n - l - 1) * M + m) * 3 + beta];
+            }
+            gsum += lam * q * ichi;
+        }
+        if (lam_out) lam_out[m * 3 + beta] = lam;
+    }
+    grad_chi[m] += gsum;
+}
+
 // P_{n-1} = T(1)/eps J_{n-1} + sum_{l=1}^{L-1} delta_l J_{n-l} - chi (G * J)_hist, AoS out
 template <typename R>
 __global__ void k_history_out(long long M, const double* __restrict__ eps,
@@ -343,6 +405,41 @@ __global__ void k_history_out(long long M, const double* __restrict__ eps,
     double P = 0.5 / eps[m] * Jring[jslot(s0, 1, jring, st) + i] - chi[m] * (double)hist[i];
     for (int l = 1; l < n_taps; ++l) P += c_taps[l] * Jring[jslot(s0, l, jring, st) + i];
     out[m * 3 + beta] = P;
+}
+
+// y = A x (FP64) on active voxels, for the setup-time eigenvalue estimate
+__global__ void k_apply64(CGArgs a, const double* __restrict__ x, double* __restrict__ y) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nact) return;
+    const int m = a.act[i];
+    double o[3];
+    applyA64(a, x, m, a.nmask[i], o);
+    y[m] = o[0];
+    y[a.M + m] = o[1];
+    y[2 * a.M + m] = o[2];
+}
+
+// partial dot products per block
+__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, long long n,
+                      double* __restrict__ part) {
+    double s = 0.0, d = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s += x[i] * y[i];
+    block_sum2(s, d);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// w = w - alpha v - beta u
+__global__ void k_axpy2(double* __restrict__ w, const double* __restrict__ v, double alpha,
+                        const double* __restrict__ u, double beta, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] -= alpha * v[i] + beta * u[i];
+}
+
+__global__ void k_scale(double* __restrict__ w, double s, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) w[i] *= s;
 }
 
 }  // namespace
@@ -378,6 +475,15 @@ void stencil_setup(mot_ctx* c) {
                 c->stencil[k + 5] = src[5] * sy * sz;
             }
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stencil, c->stencil, sizeof(double) * 27 * 6));
+    float st32[27 * 6];
+    for (int k = 0; k < 27 * 6; ++k) st32[k] = (float)c->stencil[k];
+    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_st32, st32, sizeof st32));
+    int noff[27];
+    for (int ez = -1; ez <= 1; ++ez)
+        for (int ey = -1; ey <= 1; ++ey)
+            for (int ex = -1; ex <= 1; ++ex)
+                noff[(ez + 1) * 9 + (ey + 1) * 3 + (ex + 1)] = ex + c->U * (ey + c->V * ez);
+    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_noff, noff, sizeof noff));
     double taps[MAXTAPS] = {0};
     if (c->n_taps > MAXTAPS) throw MotError{MOT_ERR_ARG, "at most 64 FIR taps are supported"};
     for (int i = 0; i < c->n_taps; ++i) taps[i] = c->taps[i];
@@ -389,40 +495,176 @@ void stencil_setup(mot_ctx* c) {
     c->cg_blocks = (int)std::min<long long>((long long)per_sm * c->nsm, std::max<long long>(need, 1));
 }
 
+namespace {
+
+// number of eigenvalues of the symmetric tridiagonal (al, be) below x (Sturm count)
+int sturm_count(const std::vector<double>& al, const std::vector<double>& be, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < al.size(); ++i) {
+        const double b2 = i ? be[i] * be[i] : 0.0;
+        q = al[i] - x - (i ? b2 / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++cnt;
+    }
+    return cnt;
+}
+
+double tridiag_eig(const std::vector<double>& al, const std::vector<double>& be, int k,
+                   double lo, double hi) {
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_count(al, be, mid) > k) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+// Spectral bounds of A = diag(1/chi) Z_0 on the active voxels by 40 Lanczos steps from a
+// seeded start vector, and the Chebyshev coefficients for the inner solve:
+// [a, b] = [theta_min, 1.02 theta_max] of the Ritz values (modes below a still
+// converge; the bound above keeps every mode in (0, a + b)).
+void chebyshev_setup(mot_ctx* c) {
+    const long long n3 = 3 * c->M;
+    const int nb = 256;
+    double *v0 = nullptr, *v1 = nullptr, *w = nullptr, *part = nullptr;
+    MOT_CUDA_TRY(cudaMalloc(&v0, sizeof(double) * n3));
+    MOT_CUDA_TRY(cudaMalloc(&v1, sizeof(double) * n3));
+    MOT_CUDA_TRY(cudaMalloc(&w, sizeof(double) * n3));
+    MOT_CUDA_TRY(cudaMalloc(&part, sizeof(double) * nb));
+    std::vector<double> al, be;
+    try {
+        std::vector<double> h(n3, 0.0), act(c->nact);
+        std::vector<int> ai(c->nact);
+        MOT_CUDA_TRY(cudaMemcpy(ai.data(), c->active, sizeof(int) * c->nact, cudaMemcpyDeviceToHost));
+        unsigned long long st = 240703323ULL;
+        double nrm = 0.0;
+        for (long long i = 0; i < c->nact; ++i)
+            for (int k = 0; k < 3; ++k) {
+                st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+                const double r = (double)(st >> 11) / 9007199254740992.0 - 0.5;
+                h[k * c->M + ai[i]] = r;
+                nrm += r * r;
+            }
+        nrm = std::sqrt(nrm);
+        for (double& x : h) x /= nrm;
+        MOT_CUDA_TRY(cudaMemcpy(v1, h.data(), sizeof(double) * n3, cudaMemcpyHostToDevice));
+        MOT_CUDA_TRY(cudaMemset(v0, 0, sizeof(double) * n3));
+        CGArgs a{};
+        a.M = c->M; a.act = c->active; a.nmask = c->nmask; a.nact = c->nact; a.diag = c->cg_diag;
+        auto dot = [&](const double* x, const double* y) {
+            k_dot<<<nb, NT, 0, c->stream>>>(x, y, n3, part);
+            MOT_LAUNCH_CHECK();
+            std::vector<double> hp(nb);
+            MOT_CUDA_TRY(cudaMemcpyAsync(hp.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost,
+                                         c->stream));
+            MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            double s = 0.0;
+            for (double x : hp) s += x;
+            return s;
+        };
+        double beta = 0.0;
+        const int blocks = (int)((n3 + NT - 1) / NT);
+        for (int j = 0; j < 40; ++j) {
+            MOT_CUDA_TRY(cudaMemsetAsync(w, 0, sizeof(double) * n3, c->stream));
+            k_apply64<<<(int)((c->nact + NT - 1) / NT), NT, 0, c->stream>>>(a, v1, w);
+            MOT_LAUNCH_CHECK();
+            const double alpha = dot(w, v1);
+            k_axpy2<<<blocks, NT, 0, c->stream>>>(w, v1, alpha, v0, beta, n3);
+            MOT_LAUNCH_CHECK();
+            al.push_back(alpha);
+            be.push_back(beta);
+            beta = std::sqrt(std::max(dot(w, w), 0.0));
+            if (!(beta > 1e-14)) break;
+            k_scale<<<blocks, NT, 0, c->stream>>>(w, 1.0 / beta, n3);
+            MOT_LAUNCH_CHECK();
+            std::swap(v0, v1);
+            std::swap(v1, w);
+        }
+    } catch (...) {
+        cudaFree(v0); cudaFree(v1); cudaFree(w); cudaFree(part);
+        throw;
+    }
+    cudaFree(v0); cudaFree(v1); cudaFree(w); cudaFree(part);
+    double lo = 1e300, hi = -1e300;
+    for (size_t i = 0; i < al.size(); ++i) {
+        const double r = std::fabs(al[i]) + (i ? std::fabs(be[i]) : 0.0) +
+                         (i + 1 < al.size() ? std::fabs(be[i + 1]) : 0.0);
+        lo = std::min(lo, al[i] - r);
+        hi = std::max(hi, al[i] + r);
+    }
+    const int k = (int)al.size();
+    const double tmin = tridiag_eig(al, be, 0, lo, hi);
+    const double tmax = tridiag_eig(al, be, k - 1, lo, hi);
+    if (!(tmin > 0.0) || !(tmax > tmin))
+        throw MotError{MOT_ERR_ARG, "diag(1/chi) Z_0 is not positive definite on this grid"};
+    const double A = tmin, B = 1.02 * tmax;
+    c->cheb_lmin = A;
+    c->cheb_lmax = B;
+    const double theta = 0.5 * (B + A), delta = 0.5 * (B - A), sigma = theta / delta;
+    const double kap = B / A;
+    const double rate = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+    int nk = (int)std::ceil(std::log(5e-6) / std::log(rate));
+    nk = std::max(4, std::min(nk, MAXCHEB));
+    c->cheb_n = nk;
+    c->cheb_log_rate = std::log(rate);
+    c->cheb_inv_theta = (float)(1.0 / theta);
+    double rho = 1.0 / sigma;
+    for (int i = 0; i < nk; ++i) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        c->cheb_c1[i] = (float)(rn * rho);
+        c->cheb_c2[i] = (float)(2.0 * rn / delta);
+        rho = rn;
+    }
+}
+
 template <typename R>
 void epilogue(mot_ctx* c, int n, const double* En, cudaStream_t s) {
     const long long tot = 3 * c->M;
     k_epilogue<R><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
-        c->M, c->eps, c->chi, En, hbuf<R>(c).hist_spatial, c->J, (int)slot_index(n, c->jring),
-        c->jring, c->n_taps, c->rhs);
+        c->M, c->vfac, En, hbuf<R>(c).hist_spatial, c->J, (int)slot_index(n, c->jring), c->jring,
+        c->n_taps, c->rhs);
     MOT_LAUNCH_CHECK();
+}
+
+CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
+    CGArgs a;
+    a.M = c->M;
+    a.act = c->active;
+    a.nmask = c->nmask;
+    a.nact = c->nact;
+    a.x = c->J + slot_index(n, c->jring) * 3 * c->M;
+    a.b = c->rhs;
+    a.diag32 = c->diag32;
+    a.diag = c->cg_diag;
+    a.r64 = c->cg_r;
+    a.r = reinterpret_cast<float4*>(c->cg32);
+    a.p = a.r + c->M;
+    a.q = a.r + 2 * c->M;
+    a.e = a.r + 3 * c->M;
+    a.red = c->red;
+    a.tol2 = c->tol * c->tol;
+    a.inv_theta = c->cheb_inv_theta;
+    a.n_cheb = c->cheb_n;
+    a.log_rate = c->cheb_log_rate;
+    for (int k = 0; k < MAXCHEB; ++k) {
+        a.c1[k] = k < c->cheb_n ? c->cheb_c1[k] : 0.f;
+        a.c2[k] = k < c->cheb_n ? c->cheb_c2[k] : 0.f;
+    }
+    a.max_iter = c->max_iter;
+    a.max_outer = 12;
+    a.step = n;
+    a.status = c->dstatus;
+    a.norm2 = norm2_out;
+    return a;
 }
 
 // rhs + CG for step n; ||J_n||^2 into norm2_out (device), J_n in ring slot n
 void solve_step(mot_ctx* c, int n, const double* En, double* norm2_out, cudaStream_t s) {
     if (c->precision == MOT_FP64) epilogue<double>(c, n, En, s);
     else epilogue<float>(c, n, En, s);
-    CGArgs a;
-    a.M = c->M; a.U = c->U; a.V = c->V; a.W = c->W;
-    a.act = c->active;
-    a.nact = c->nact;
-    a.x = c->J + slot_index(n, c->jring) * 3 * c->M;
-    a.b = c->rhs;
-    a.r64 = c->cg_r;
-    a.r = c->cg32;
-    a.p = c->cg32 + 3 * c->M;
-    a.q = c->cg32 + 6 * c->M;
-    a.e = c->cg32 + 9 * c->M;
-    a.diag = c->cg_diag;
-    a.red = c->red;
-    a.tol2 = c->tol * c->tol;
-    a.tin2 = 1e-10f;
-    a.max_inner = 40;
-    a.max_iter = c->max_iter;
-    a.max_outer = 12;
-    a.step = n;
-    a.status = c->dstatus;
-    a.norm2 = norm2_out;
+    CGArgs a = make_cg_args(c, n, norm2_out);
     void* args[] = {&a};
     MOT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_cg, c->cg_blocks, NT, args, 0, s));
 }
@@ -444,6 +686,27 @@ void history_out(mot_ctx* c, int n, double* out_dev, cudaStream_t s) {
             c->M, c->eps, c->chi, c->h32.hist_spatial, c->J, (int)slot_index(n, c->jring), c->jring,
             c->n_taps, out_dev);
     MOT_LAUNCH_CHECK();
+}
+
+// one adjoint step: tau = adjoint time (ring index), n = N + 1 - tau (forward time)
+void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double* J_aos,
+                  double* grad_chi, double* lam_out, double* norm2_out, cudaStream_t s) {
+    const long long tot = 3 * c->M;
+    const int s0 = (int)slot_index(tau, c->jring);
+    if (c->precision == MOT_FP64)
+        k_epilogue_adj<double><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
+            c->M, c->vfac, g_aos, c->h64.hist_spatial, c->J, s0, c->jring, c->n_taps, c->rhs);
+    else
+        k_epilogue_adj<float><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
+            c->M, c->vfac, g_aos, c->h32.hist_spatial, c->J, s0, c->jring, c->n_taps, c->rhs);
+    MOT_LAUNCH_CHECK();
+    CGArgs a = make_cg_args(c, tau, norm2_out);
+    void* args[] = {&a};
+    MOT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_cg, c->cg_blocks, NT, args, 0, s));
+    k_adj_post<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(
+        c->M, c->vfac, c->J + (long long)s0 * 3 * c->M, J_aos, n, c->n_taps, grad_chi, lam_out);
+    MOT_LAUNCH_CHECK();
+    c->stats.launches += 3;
 }
 
 void write_aos(mot_ctx* c, int n, double* out_dev, cudaStream_t s) {

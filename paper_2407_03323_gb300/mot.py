@@ -26,14 +26,15 @@ PRECISIONS = {"fp64": 0, "fp32_history": 1}
 SCHEMES = {"direct": 0, "blocked": 1}
 
 EXPORTS = ["mot_create", "mot_destroy", "mot_set_excitation", "mot_plane_wave", "mot_march",
-           "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
+           "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_last_error"]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("mac_launches", ctypes.c_longlong),
-                ("steps", ctypes.c_longlong), ("cg_iters", ctypes.c_longlong),
-                ("ms_fft_fwd", ctypes.c_double), ("ms_mac", ctypes.c_double),
+                ("far_launches", ctypes.c_longlong), ("steps", ctypes.c_longlong),
+                ("cg_iters", ctypes.c_longlong), ("ms_fft_fwd", ctypes.c_double),
+                ("ms_far", ctypes.c_double), ("ms_mac", ctypes.c_double),
                 ("ms_fft_inv", ctypes.c_double), ("ms_solve", ctypes.c_double)]
 
 
@@ -65,6 +66,7 @@ def load_library(path=LIB_PATH):
     lib.mot_plane_wave.argtypes = [P, P, P, D, D, D, I, I, P, P]
     lib.mot_march.argtypes = [P, I, P, P]
     lib.mot_eval_history.argtypes = [P, I, P, P, P]
+    lib.mot_adjoint.argtypes = [P, I, P, P, P, P, P]
     lib.mot_get_table.argtypes = [P, I, I, P]
     lib.mot_get_spectrum.argtypes = [P, I, P]
     lib.mot_get_info.argtypes = [P, P, P, P, P, P, P]
@@ -135,6 +137,9 @@ class Context:
             raise MotError(st, lib.mot_last_error(None).decode())
         self._h = out
         self._lib = lib
+        self._scheme = scheme
+        self._precision = precision
+        self._block = int(block)
         info = self.info()
         self.ell = info["ell"]
         self.P = info["P"]
@@ -187,6 +192,20 @@ class Context:
         self._check(self._lib.mot_march(self._h, n_steps, _ptr(out), _stream(stream)))
         return out
 
+    def adjoint(self, J, dO_dJ, want_lambda=False, stream=None):
+        """dO/d eps_r per voxel by the adjoint march (mot_adjoint); returns grad [W][V][U]
+        (and lambda [N][M][3] if want_lambda)."""
+        if isinstance(J, np.ndarray):
+            J = np.ascontiguousarray(J, dtype=np.float64)
+        if isinstance(dO_dJ, np.ndarray):
+            dO_dJ = np.ascontiguousarray(dO_dJ, dtype=np.float64)
+        n = J.shape[0]
+        grad = np.zeros(self.shape)
+        lam = np.zeros((n, self.M, 3)) if want_lambda else None
+        self._check(self._lib.mot_adjoint(self._h, n, _ptr(J), _ptr(dO_dJ), grad.ctypes.data,
+                                          _ptr(lam), _stream(stream)))
+        return (grad, lam) if want_lambda else grad
+
     def eval_history(self, J_hist, out=None, stream=None):
         J = J_hist
         if isinstance(J, np.ndarray):
@@ -207,6 +226,17 @@ class Context:
         Pu, Pv, Pw = self.P
         out = np.zeros((6, Pw // 2 + 1, Pv // 2 + 1, Pu // 2 + 1))
         self._check(self._lib.mot_get_spectrum(self._h, l, out.ctypes.data))
+        return out
+
+    @property
+    def levels(self):
+        """Block lengths S of the blocked scheme (empty for the direct scheme)."""
+        if getattr(self, "_scheme", "direct") != "blocked":
+            return []
+        out, S = [], self._block
+        while S <= self.ell:
+            out.append(S)
+            S *= 2
         return out
 
     def info(self):
@@ -231,5 +261,7 @@ class Context:
         self._check(self._lib.mot_get_stats(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_}
 
-    def set_solver(self, tol=1e-13, max_iter=200, growth_limit=1e12):
+    def set_solver(self, tol=None, max_iter=200, growth_limit=1e12):
+        if tol is None:
+            tol = 1e-13 if self._precision == "fp64" else 1e-10
         self._check(self._lib.mot_set_solver(self._h, tol, max_iter, growth_limit))

@@ -1,0 +1,109 @@
+"""Failure detection of the march, made on the host side: an iteration cap the solver
+cannot meet, a growth limit the pulse must exceed, invalid arguments.  Nothing here
+faults, traps or hangs a GPU; every case returns a status the caller reads."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mot():
+    from paper_2407_03323_gb300 import build, mot as m
+    if not os.path.exists(m.LIB_PATH):
+        build.build()
+    m.load_library()
+    return m
+
+
+def _pulse_ctx(mot, N=6, **kw):
+    eps = wl.cube(N, 5.0)
+    p = wl.pulse(N, 5.0)
+    ctx = mot.Context(eps, **kw)
+    E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 60, 1, 48)
+    ctx.set_excitation(E)
+    return ctx
+
+
+def test_not_converged_status_and_recovery(mot):
+    """An iteration cap below what the solve needs gives MOT_ERR_NOT_CONVERGED with the
+    step recorded; the context stays usable and converges again with the cap lifted."""
+    ctx = _pulse_ctx(mot)
+    ctx.set_solver(tol=1e-13, max_iter=1)
+    with pytest.raises(mot.MotError) as ei:
+        ctx.march(8)
+    assert ei.value.status == mot.MOT_ERR_NOT_CONVERGED
+    info = ctx.info()
+    assert 1 <= info["fail_step"] <= 8
+    ctx.set_solver(tol=1e-13, max_iter=200)
+    ctx.march(8)
+    assert ctx.info()["n_done"] == 16
+    ctx.close()
+
+
+def test_unstable_status_on_growth(mot):
+    """A growth limit just above 1 trips on the rising edge of the pulse: the monitor
+    reports MOT_ERR_UNSTABLE and the step where it happened."""
+    ctx = _pulse_ctx(mot)
+    ctx.set_solver(tol=1e-13, max_iter=200, growth_limit=1.0001)
+    with pytest.raises(mot.MotError) as ei:
+        ctx.march(48)
+    assert ei.value.status == mot.MOT_ERR_UNSTABLE
+    assert ctx.info()["fail_step"] > 0
+    ctx.close()
+
+
+def test_bad_arguments(mot):
+    with pytest.raises(mot.MotError) as ei:
+        mot.Context(wl.cube(4, 0.5))
+    assert ei.value.status == mot.MOT_ERR_ARG
+    with pytest.raises(mot.MotError) as ei:
+        mot.Context(wl.cube(4, 3.0), scheme="blocked", block=3)
+    assert ei.value.status == mot.MOT_ERR_ARG
+    with mot.Context(wl.cube(4, 3.0)) as ctx:
+        with pytest.raises(mot.MotError) as ei:
+            ctx.march(0)
+        assert ei.value.status == mot.MOT_ERR_ARG
+        with pytest.raises(mot.MotError) as ei:
+            ctx.eval_history(np.zeros((ctx.ell + 1, 64, 3)))
+        assert ei.value.status == mot.MOT_ERR_ARG
+
+
+def test_vacuum_voxels_stay_zero(mot):
+    """Voxels with eps_r = 1 (chi = 0) carry no current (reading R5)."""
+    N = 8
+    eps = wl.sphere(N, 12.0)
+    p = wl.pulse(N, 12.0)
+    with mot.Context(eps) as ctx:
+        E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 80, 1, 64)
+        ctx.set_excitation(E)
+        J = ctx.march(64)
+    out = eps.reshape(-1) == 1.0
+    assert np.abs(J[:, ~out]).max() > 0
+    assert np.abs(J[:, out]).max() == 0.0
+
+
+@pytest.mark.parametrize("precision,factors,tol", [("fp64", (1e-60, 1e60), 1e-12),
+                                                    ("fp32_history", (1e-20, 1e20), 1e-6)])
+def test_tiny_and_huge_excitations_scale_linearly(mot, precision, factors, tol):
+    """The march is linear: an excitation scaled by f gives the current scaled by f.
+    The solver normalises residuals in FP64 before its FP32 inner iterations, so tiny
+    or huge right-hand sides neither underflow nor overflow there.  The FP32-history
+    variant stores the spectra of J in FP32, so its range is that of FP32 (|J| within
+    about 1e-30 .. 1e30); FP64 is exercised at 1e+-60."""
+    N = 6
+    eps = wl.cube(N, 4.0)
+    p = wl.pulse(N, 4.0)
+    res = {}
+    for f in (1.0,) + tuple(factors):
+        with mot.Context(eps, precision=precision, scheme="blocked", block=4) as ctx:
+            E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 40, 1, 40)
+            ctx.set_excitation(E * f)
+            res[f] = ctx.march(40)
+    for f in factors:
+        assert np.isfinite(res[f]).all()
+        assert np.linalg.norm(res[f] / f - res[1.0]) < tol * np.linalg.norm(res[1.0])

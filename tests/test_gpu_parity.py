@@ -207,3 +207,53 @@ def test_march_in_chunks_equals_one_call(mot, cube8_oracle):
             parts.append(ctx.march(32))
         J2 = np.concatenate(parts)
     assert np.array_equal(J1, J2)
+
+
+# ---------------------------------------------------------------- blocked temporal scheme
+
+@pytest.mark.parametrize("block", [2, 4, 8])
+def test_march_cube8_blocked_matches_oracle(mot, cube8_oracle, block):
+    """Lags >= B through block Toeplitz products with temporal FFTs (Secs. 4-5) give
+    the oracle's march (8^3: ell = 15, levels up to S = 8)."""
+    o = cube8_oracle
+    with mot.Context(o["cfg"]["eps_r"], o["cfg"]["taps"], scheme="blocked", block=block) as ctx:
+        ctx.set_excitation(o["E"])
+        J = ctx.march(o["E"].shape[0])
+    assert rel_l2(J, o["J"]) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_history"])
+def test_history_blocked_matches_direct_sum(mot, cube8_oracle, precision):
+    from oracle import march
+    o = cube8_oracle
+    eps = o["cfg"]["eps_r"].copy()
+    eps[1:6, 2:4, 0:5] = 7.0
+    taps = wl.fir_taps("fir3", 0.1)
+    rng = np.random.default_rng(13)
+    ell = o["ell"]
+    M = eps.size
+    Jh = rng.normal(size=(ell, M, 3))
+    with mot.Context(eps, taps, precision=precision, scheme="blocked", block=2) as ctx:
+        P = ctx.eval_history(Jh)
+    ref = march.history_at(o["G"], eps, taps, Jh, list(range(M)))
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    assert rel_l2(P, ref) < tol
+
+
+def test_blocked_equals_direct_sphere32(mot):
+    """32^3 sphere with the 9-tap FIR, 200 steps: blocked (B = 8, levels 8..32) and
+    direct march agree to rounding in FP64 and to 1e-6 in FP32-history."""
+    cfg = wl.config("sphere32")
+    eps, taps, p = cfg["eps_r"], cfg["taps"], cfg["pulse"]
+    steps = 200
+    out = {}
+    for scheme, prec in (("direct", "fp64"), ("blocked", "fp64"), ("blocked", "fp32_history")):
+        with mot.Context(eps, taps, precision=prec, scheme=scheme, block=8) as ctx:
+            E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 150, 1,
+                               steps)
+            ctx.set_excitation(E)
+            out[(scheme, prec)] = ctx.march(steps)
+    ref = out[("direct", "fp64")]
+    assert np.linalg.norm(ref) > 0
+    assert rel_l2(out[("blocked", "fp64")], ref) < 1e-12
+    assert rel_l2(out[("blocked", "fp32_history")], ref) < 1e-5

@@ -150,3 +150,50 @@ def test_excitation_quadrature_converged():
     a = excitation.tested_excitation(cfg["eps_r"], cfg["pulse"], 4, n_first=95, npts=8)
     b = excitation.tested_excitation(cfg["eps_r"], cfg["pulse"], 4, n_first=95, npts=12)
     assert np.abs(a - b).max() < 1e-14 * np.abs(a).max()
+
+
+def test_adjoint_duality():
+    """For any g and E: sum_n <g_n, J_n> = sum_n <lambda_n, E_n> when Z J = E and
+    Z^T lambda = g (the adjoint march solves the transposed system)."""
+    from oracle import adjoint
+    eps_r, G, E, taps, _ = _small(3, 7.0, steps=30)
+    taps = wl.fir_taps("fir3", 0.05)
+    J = march.march(G, eps_r, taps, E)
+    g = np.random.default_rng(2).normal(size=J.shape)
+    lam = adjoint.adjoint(G, eps_r, taps, g)
+    lhs = np.sum(g * J)
+    rhs = np.sum(lam * E)
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    """dO/deps_m of O = sum_n <g_n, J_n(eps)> by the adjoint against central differences
+    of two forward marches (E depends on eps through chi as well)."""
+    from oracle import adjoint
+    N = 3
+    rng = np.random.default_rng(4)
+    eps_r = 3.0 + 4.0 * rng.uniform(size=(N, N, N))
+    taps = wl.fir_taps("fir3", 0.05)
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, ell + 1)
+    pulse = wl.pulse(N, 5.0)
+    steps = 30
+    g = rng.normal(size=(steps, N ** 3, 3))
+
+    def objective(eps):
+        E = excitation.tested_excitation(eps, pulse, steps)
+        return np.sum(g * march.march(G, eps, taps, E))
+
+    E = excitation.tested_excitation(eps_r, pulse, steps)
+    e_inc = excitation.tested_excitation(eps_r, pulse, steps, with_chi=False)
+    J = march.march(G, eps_r, taps, E)
+    lam = adjoint.adjoint(G, eps_r, taps, g)
+    grad = adjoint.gradient_eps(G, eps_r, taps, e_inc, J, lam)
+    h = 1e-5
+    for m in (0, 13, 26):
+        ep = eps_r.copy().reshape(-1)
+        em = eps_r.copy().reshape(-1)
+        ep[m] += h
+        em[m] -= h
+        fd = (objective(ep.reshape(eps_r.shape)) - objective(em.reshape(eps_r.shape))) / (2 * h)
+        assert abs(fd - grad[m]) < 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max())
