@@ -70,6 +70,7 @@ void free_all(mot_ctx* c) {
     cudaFree(c->cg32);
     cudaFree(c->active);
     cudaFree(c->nmask);
+    cudaFree(c->tiles);
     cudaFree(c->diag32);
     cudaFree(c->vfac);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
@@ -116,7 +117,7 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
     };
     if (!grid || !h || !eps_r || !out) return fail(MOT_ERR_ARG, "null argument");
     for (int a = 0; a < 3; ++a)
-        if (grid[a] < 1 || grid[a] > 4096) return fail(MOT_ERR_ARG, "grid sizes must be in 1..4096");
+        if (grid[a] < 1 || grid[a] > 1024) return fail(MOT_ERR_ARG, "grid sizes must be in 1..1024");
     if ((long long)grid[0] * grid[1] * grid[2] > (1LL << 30))
         return fail(MOT_ERR_ARG, "at most 2^30 voxels");
     if (!(h[0] > 0) || h[0] != h[1] || h[0] != h[2])
@@ -221,6 +222,24 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
                                         cudaMemcpyHostToDevice));
                 MOT_CUDA_TRY(cudaMemcpy(c->nmask, nm.data(), sizeof(int) * c->nact,
                                         cudaMemcpyHostToDevice));
+            }
+            {   // 8^3 tiles that hold at least one active voxel
+                std::vector<int> tl;
+                for (int z0 = 0; z0 < c->W; z0 += 8)
+                    for (int y0 = 0; y0 < c->V; y0 += 8)
+                        for (int x0 = 0; x0 < c->U; x0 += 8) {
+                            bool any = false;
+                            for (int z = z0; z < std::min(z0 + 8, c->W) && !any; ++z)
+                                for (int y = y0; y < std::min(y0 + 8, c->V) && !any; ++y)
+                                    for (int x = x0; x < std::min(x0 + 8, c->U) && !any; ++x)
+                                        any = chi[((long long)z * c->V + y) * c->U + x] > 0.0;
+                            if (any) tl.push_back(x0 | (y0 << 10) | (z0 << 20));
+                        }
+                c->ntiles = (int)tl.size();
+                MOT_CUDA_TRY(cudaMalloc(&c->tiles, sizeof(int) * std::max<size_t>(tl.size(), 1)));
+                if (!tl.empty())
+                    MOT_CUDA_TRY(cudaMemcpy(c->tiles, tl.data(), sizeof(int) * tl.size(),
+                                            cudaMemcpyHostToDevice));
             }
             std::vector<float> d32(M);
             std::vector<double> vf(4 * M);

@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(NT) k_fwd_x(const double* __restrict__ in, int
         b0[j * ld + t] = z;
     }
     __syncthreads();
-    C* res = fft_tile(b0, b1, P, rl.r, rl.n, TB, ld, stw, -1);
+    C* res = fft_tile<C, TB>(b0, b1, P, rl.r, rl.n, ld, stw, -1);
     // split: A = (Z[k] + conj Z[P-k]) / 2, B = -i (Z[k] - conj Z[P-k]) / 2
     for (int it = threadIdx.x; it < TB * Hu; it += blockDim.x) {
         const int t = it / Hu, k = it % Hu;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NT) k_inv_x(const typename CT<R>::c* __restric
         }
     }
     __syncthreads();
-    C* res = fft_tile(b0, b1, P, rl.r, rl.n, TB, ld, stw, +1);
+    C* res = fft_tile<C, TB>(b0, b1, P, rl.r, rl.n, ld, stw, +1);
     for (int it = threadIdx.x; it < TB * U; it += blockDim.x) {
         const int t = it / U, j = it % U;
         const long long pr = pair0 + t;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(NT) k_mid(const typename CT<R>::c* __restrict_
         b0[j * ld + t] = z;
     }
     __syncthreads();
-    C* res = fft_tile(b0, b1, P, rl.r, rl.n, TB, ld, stw, a.dir);
+    C* res = fft_tile<C, TB>(b0, b1, P, rl.r, rl.n, ld, stw, a.dir);
     for (int it = threadIdx.x; it < a.n_out * TB; it += blockDim.x) {
         const int j = it / TB, t = it % TB;
         if (ku0 + t < a.Hu) dst[j * a.out_a + t] = res[j * ld + t];

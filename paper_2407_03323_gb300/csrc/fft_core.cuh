@@ -73,44 +73,50 @@ __device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
     }
 }
 
-template <typename C, int R>
+// one Stockham stage of radix R over TB lines (TB known at compile time); Ns is the
+// product of the earlier radices; j / Ns is taken as trunc((j + 1/2) / Ns) in FP32,
+// exact for j < 2^20
+template <typename C, int R, int TB>
 __device__ __forceinline__ void stage(const C* __restrict__ x, C* __restrict__ y, int P, int Ns,
-                                      int TB, int ld, const C* tw, int dir) {
+                                      int ld, const C* tw, int dir) {
     const int nb = P / R;
     const int items = nb * TB;
+    const int tstep = P / (Ns * R);
+    const float inv_ns = 1.0f / (float)Ns;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int t = it % TB, j = it / TB;
-        const int k = j % Ns;
+        const int jq = __float2int_rz(((float)j + 0.5f) * inv_ns);
+        const int k = j - jq * Ns;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = x[(j + r * nb) * ld + t];
         if (Ns > 1) {
-            const int tstep = P / (Ns * R);
+            const int kt = k * tstep;      // r * kt < P
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid(tw, (r * k * tstep) % P, dir));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid(tw, r * kt, dir));
         }
         dft_small<C, R>(v, tw, P, dir);
-        const int base = (j / Ns) * Ns * R + k;
+        const int base = jq * Ns * R + k;
 #pragma unroll
         for (int r = 0; r < R; ++r) y[(base + r * Ns) * ld + t] = v[r];
     }
 }
 
-// runs all stages; returns the buffer holding the result
-template <typename C>
-__device__ C* fft_tile(C* b0, C* b1, int P, const int* rad, int nrad, int TB, int ld,
-                       const C* tw, int dir) {
+// runs all stages over TB lines of length P; returns the buffer holding the result
+template <typename C, int TB>
+__device__ C* fft_tile(C* b0, C* b1, int P, const int* rad, int nrad, int ld, const C* tw,
+                       int dir) {
     int Ns = 1;
     C* x = b0;
     C* y = b1;
     for (int s = 0; s < nrad; ++s) {
         const int R = rad[s];
         switch (R) {
-            case 2: stage<C, 2>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 3: stage<C, 3>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 4: stage<C, 4>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 5: stage<C, 5>(x, y, P, Ns, TB, ld, tw, dir); break;
-            case 7: stage<C, 7>(x, y, P, Ns, TB, ld, tw, dir); break;
+            case 2: stage<C, 2, TB>(x, y, P, Ns, ld, tw, dir); break;
+            case 3: stage<C, 3, TB>(x, y, P, Ns, ld, tw, dir); break;
+            case 4: stage<C, 4, TB>(x, y, P, Ns, ld, tw, dir); break;
+            case 5: stage<C, 5, TB>(x, y, P, Ns, ld, tw, dir); break;
+            case 7: stage<C, 7, TB>(x, y, P, Ns, ld, tw, dir); break;
         }
         __syncthreads();
         Ns *= R;

@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
 }
 
 // temporal spectra of level S: H(w) = sum_{m=0}^{lmax-S} Ghat_{S+m} exp(-2 pi i w m / (2S)),
-// w = 0..S (the rest follows by H(2S - w) = conj H(w)); out [w][octant bin][6]
+// w = 0..S (the rest follows by H(2S - w) = conj H(w)); out [w][6][octant bin], one
+// plane per component so that a warp over consecutive bins reads one contiguous run
 template <typename R>
 __global__ void k_level_spec(const R* __restrict__ ghat, long long noct, int S, int lmax,
                              const double2* __restrict__ tw, typename CT<R>::c* __restrict__ out) {
@@ -155,21 +156,23 @@ __global__ void k_level_spec(const R* __restrict__ ghat, long long noct, int S, 
             acc[c].y += g * t.y;
         }
     }
-    C* op = out + ((long long)w * noct + o) * 6;
+    C* op = out + (long long)w * 6 * noct + o;
     for (int c = 0; c < 6; ++c) {
         C v;
         v.x = acc[c].x;
         v.y = acc[c].y;
-        op[c] = v;
+        op[c * noct] = v;
     }
 }
+
+constexpr int kMaxLevel = 256;   // longest level S (window 2S in shared memory)
 
 template <typename R> struct FarArgs {
     typedef typename CT<R>::c C;
     const C* ring;
     int hring;
     long long nbins, noct;
-    const C* H;          // level spectra [S+1][noct][6]
+    const C* H;          // level spectra [S+1][6][noct]
     C* acc;              // [smax][3][nbins]
     int smax;
     int n0, S, lmax;
@@ -209,33 +212,41 @@ __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
     const R sxy = fv ? (R)-1 : (R)1;
     const R sxz = fw ? (R)-1 : (R)1;
     const R syz = (fv != fw) ? (R)-1 : (R)1;
-    load_tw(stw, a.tw, P);
+    // ring slot of every window time (-1: older than the level's lags or before t = 1)
+    // and accumulator slot of every output time
+    __shared__ int s_in[2 * kMaxLevel];
+    __shared__ int s_out[kMaxLevel];
     const int tfirst = max(1, a.n0 - a.lmax);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int time = a.n0 - P + i;
+        s_in[i] = time >= tfirst ? time % a.hring : -1;
+        if (i < a.S) s_out[i] = (a.n0 + i) % a.smax;
+    }
+    load_tw(stw, a.tw, P);
+    __syncthreads();
     for (int it = threadIdx.x; it < P * L3; it += blockDim.x) {
         const int i = it / L3, t = it % L3;
         const int comp = t / TB, bb = t % TB;
-        const int time = a.n0 - P + i;
+        const int slot = s_in[i];
         C v;
         v.x = 0; v.y = 0;
-        if (time >= tfirst && ku0 + bb < a.Hu) {
-            const long long slot = time % a.hring;
-            v = a.ring[(slot * 3 + comp) * a.nbins + row + bb];
-        }
+        if (slot >= 0 && ku0 + bb < a.Hu)
+            v = a.ring[((long long)slot * 3 + comp) * a.nbins + row + bb];
         b0[i * ld + t] = v;
     }
     __syncthreads();
-    C* X = fft_tile(b0, b1, P, a.rl.r, a.rl.n, L3, ld, stw, -1);
+    C* X = fft_tile<C, L3>(b0, b1, P, a.rl.r, a.rl.n, ld, stw, -1);
     C* other = (X == b0) ? b1 : b0;
     for (int it = threadIdx.x; it < P * TB; it += blockDim.x) {
         const int w = it / TB, bb = it % TB;
         if (ku0 + bb >= a.Hu) continue;
         const bool cj = w > a.S;
         const int ws = cj ? P - w : w;
-        const C* hp = a.H + ((long long)ws * a.noct + orow_base + bb) * 6;
+        const C* hp = a.H + (long long)ws * 6 * a.noct + orow_base + bb;
         C h[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            h[c] = hp[c];
+            h[c] = hp[c * a.noct];
             if (cj) h[c].y = -h[c].y;
         }
         h[3].x *= sxy; h[3].y *= sxy;
@@ -248,13 +259,13 @@ __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
         xp[2 * TB] = cadd(cadd(cmul(h[4], x0), cmul(h[5], x1)), cmul(h[2], x2));
     }
     __syncthreads();
-    C* Y = fft_tile(X, other, P, a.rl.r, a.rl.n, L3, ld, stw, +1);
+    C* Y = fft_tile<C, L3>(X, other, P, a.rl.r, a.rl.n, ld, stw, +1);
     const R scale = (R)1 / (R)P;
     for (int it = threadIdx.x; it < a.S * L3; it += blockDim.x) {
         const int j = it / L3, t = it % L3;
         const int comp = t / TB, bb = t % TB;
         if (ku0 + bb >= a.Hu) continue;
-        const long long slot = (long long)((a.n0 + j) % a.smax);
+        const long long slot = s_out[j];
         C* dst = a.acc + (slot * 3 + comp) * a.nbins + row + bb;
         const C y = Y[(a.S + j) * ld + t];
         C v;
@@ -354,13 +365,289 @@ template <typename R> const typename CT<R>::c* twtab(const AxisFFT& a);
 template <> const double2* twtab<double>(const AxisFFT& a) { return a.tw64; }
 template <> const float2* twtab<float>(const AxisFFT& a) { return a.tw32; }
 
+// ---------------------------------------------------------------- register variant
+// For 2S <= 64: one thread per (bin, component) line.  A block is three warps (warp =
+// component) over 32 consecutive bins of one rfft row.  Each thread loads its 2S window
+// samples (coalesced across the warp), runs an unrolled radix-2 DIF FFT in registers
+// (output in bit-reversed order), the three spectra are exchanged through shared memory
+// for the 3x3 product (frequency of slot i is bitrev(i)), and an unrolled radix-2 DIT
+// inverse (bit-reversed input, natural output) leaves the block outputs in registers.
+template <int P> __host__ __device__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1, k = P >> 1; b < P; b <<= 1, k >>= 1)
+        if (i & b) r |= k;
+    return r;
+}
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E> struct Unroll {
+    template <typename F> __device__ __forceinline__ static void run(F&& f) {
+        f(std::integral_constant<int, B>());
+        Unroll<B + 1, E>::run(f);
+    }
+};
+template <int E> struct Unroll<E, E> {
+    template <typename F> __device__ __forceinline__ static void run(F&&) {}
+};
+
+// Lines of length P = T * Q are split over T threads; thread t holds positions
+// t Q .. t Q + Q - 1 of the (natural- or bit-reversed-order) line.  Stages whose span
+// reaches across threads exchange values with the partner thread by warp shuffles
+// (lane = t * (32 / T) + line); the others are register-local.  Twiddles index the
+// table of P roots with the stage's stride.
+
+// local DIF stage of span LEN (<= Q) over the thread's Q values
+template <typename C, int Q, int P, int LEN>
+__device__ __forceinline__ void dif_local(C* x, const C* __restrict__ tw, int dir) {
+    constexpr int half = LEN / 2, ts = P / LEN;
+    Unroll<0, Q / 2>::run([&](auto q) {
+        constexpr int st = (decltype(q)::value / half) * LEN;
+        constexpr int k = decltype(q)::value % half;
+        const C a = x[st + k], b = x[st + k + half];
+        x[st + k] = cadd(a, b);
+        C d = csub(a, b);
+        if (k) {
+            C w = tw[k * ts];
+            if (dir > 0) w.y = -w.y;
+            d = cmul(d, w);
+        }
+        x[st + k + half] = d;
+    });
+}
+
+template <typename C, int Q, int P, int LEN>
+__device__ __forceinline__ void dit_local(C* x, const C* __restrict__ tw, int dir) {
+    constexpr int half = LEN / 2, ts = P / LEN;
+    Unroll<0, Q / 2>::run([&](auto q) {
+        constexpr int st = (decltype(q)::value / half) * LEN;
+        constexpr int k = decltype(q)::value % half;
+        const C a = x[st + k];
+        C b = x[st + k + half];
+        if (k) {
+            C w = tw[k * ts];
+            if (dir > 0) w.y = -w.y;
+            b = cmul(b, w);
+        }
+        x[st + k] = cadd(a, b);
+        x[st + k + half] = csub(a, b);
+    });
+}
+
+__device__ __forceinline__ float2 shfl_c(float2 v, int mask) {
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, mask);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, mask);
+    return v;
+}
+__device__ __forceinline__ double2 shfl_c(double2 v, int mask) {
+    v.x = __shfl_xor_sync(0xffffffffu, v.x, mask);
+    v.y = __shfl_xor_sync(0xffffffffu, v.y, mask);
+    return v;
+}
+
+// cross-thread DIF stage: span LEN = 2 * HT * Q, partner thread t ^ HT
+template <typename C, int Q, int T, int HT>
+__device__ __forceinline__ void dif_cross(C* x, const C* __restrict__ tw, int dir, int t) {
+    constexpr int P = Q * T, LEN = 2 * HT * Q, ts = P / LEN;
+    const bool upper = (t & HT) == 0;
+    const int base = ((t & ~HT) * Q) % LEN;
+    Unroll<0, Q>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        const C mine = x[j];
+        const C other = shfl_c(mine, HT * (32 / T));
+        if (upper) {
+            x[j] = cadd(mine, other);
+        } else {
+            C w = tw[(base + j) * ts];
+            if (dir > 0) w.y = -w.y;
+            x[j] = cmul(csub(other, mine), w);
+        }
+    });
+}
+
+template <typename C, int Q, int T, int HT>
+__device__ __forceinline__ void dit_cross(C* x, const C* __restrict__ tw, int dir, int t) {
+    constexpr int P = Q * T, LEN = 2 * HT * Q, ts = P / LEN;
+    const bool upper = (t & HT) == 0;
+    const int base = ((t & ~HT) * Q) % LEN;
+    Unroll<0, Q>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        C send = x[j];
+        if (!upper) {
+            C w = tw[(base + j) * ts];
+            if (dir > 0) w.y = -w.y;
+            send = cmul(send, w);
+        }
+        const C recv = shfl_c(send, HT * (32 / T));
+        x[j] = upper ? cadd(send, recv) : csub(recv, send);
+    });
+}
+
+template <typename C, int Q, int T, int LEN> struct DifLoc {
+    __device__ __forceinline__ static void run(C* x, const C* tw, int dir) {
+        dif_local<C, Q, Q * T, LEN>(x, tw, dir);
+        DifLoc<C, Q, T, LEN / 2>::run(x, tw, dir);
+    }
+};
+template <typename C, int Q, int T> struct DifLoc<C, Q, T, 1> {
+    __device__ __forceinline__ static void run(C*, const C*, int) {}
+};
+template <typename C, int Q, int T, int LEN> struct DitLoc {
+    __device__ __forceinline__ static void run(C* x, const C* tw, int dir) {
+        dit_local<C, Q, Q * T, LEN>(x, tw, dir);
+        DitLoc<C, Q, T, LEN * 2>::run(x, tw, dir);
+    }
+};
+template <typename C, int Q, int T> struct DitLoc<C, Q, T, 2 * Q> {
+    __device__ __forceinline__ static void run(C*, const C*, int) {}
+};
+template <typename C, int Q, int T, int HT> struct DifCross {
+    __device__ __forceinline__ static void run(C* x, const C* tw, int dir, int t) {
+        dif_cross<C, Q, T, HT>(x, tw, dir, t);
+        DifCross<C, Q, T, HT / 2>::run(x, tw, dir, t);
+    }
+};
+template <typename C, int Q, int T> struct DifCross<C, Q, T, 0> {
+    __device__ __forceinline__ static void run(C*, const C*, int, int) {}
+};
+template <typename C, int Q, int T, int HT> struct DitCross {
+    __device__ __forceinline__ static void run(C* x, const C* tw, int dir, int t) {
+        dit_cross<C, Q, T, HT>(x, tw, dir, t);
+        DitCross<C, Q, T, HT * 2>::run(x, tw, dir, t);
+    }
+};
+template <typename C, int Q, int T> struct DitCross<C, Q, T, T> {
+    __device__ __forceinline__ static void run(C*, const C*, int, int) {}
+};
+
+// natural order in, bit-reversed out: cross stages (span > Q) first, then local
+template <typename C, int Q, int T>
+__device__ __forceinline__ void fft_dif_reg(C* x, const C* __restrict__ tw, int dir, int t) {
+    DifCross<C, Q, T, T / 2>::run(x, tw, dir, t);
+    DifLoc<C, Q, T, Q>::run(x, tw, dir);
+}
+// bit-reversed in, natural order out: local stages first, then cross
+template <typename C, int Q, int T>
+__device__ __forceinline__ void fft_dit_reg(C* x, const C* __restrict__ tw, int dir, int t) {
+    DitLoc<C, Q, T, 2>::run(x, tw, dir);
+    DitCross<C, Q, T, 1>::run(x, tw, dir, t);
+}
+
+template <typename R, int Q, int T>
+__global__ void __launch_bounds__(96) k_far_reg(FarArgs<R> a) {
+    typedef typename CT<R>::c C;
+    constexpr int P = Q * T, S = P / 2, NB = 32 / T;   // NB bins per warp
+    __shared__ C sX[P][3][NB];
+    __shared__ C stw[P];
+    __shared__ int s_in[P];
+    __shared__ int s_out[S];
+    const int comp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t = lane / NB, line = lane % NB;
+    const int ut = blockIdx.x % a.ntile;
+    const int rest = blockIdx.x / a.ntile;
+    const int mirror = rest & 3;
+    const int orow = rest >> 2;
+    const int kv_o = orow % a.Hv, kw_o = orow / a.Hv;
+    const bool fv = (mirror & 1) != 0, fw = (mirror & 2) != 0;
+    const bool mv = kv_o > 0 && 2 * kv_o < a.Pv;
+    const bool mw = kw_o > 0 && 2 * kw_o < a.Pw;
+    if ((fv && !mv) || (fw && !mw)) return;
+    const int kv = fv ? a.Pv - kv_o : kv_o;
+    const int kw = fw ? a.Pw - kw_o : kw_o;
+    const int ku = ut * NB + line;
+    const bool live = ku < a.Hu;
+    const long long row = ((long long)kw * a.Pv + kv) * a.Hu + ku;
+    const long long obin = ((long long)kw_o * a.Hv + kv_o) * a.Hu + ku;
+    const int tfirst = max(1, a.n0 - a.lmax);
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int time = a.n0 - P + i;
+        s_in[i] = time >= tfirst ? time % a.hring : -1;
+        stw[i] = a.tw[i];
+        if (i < S) s_out[i] = (a.n0 + i) % a.smax;
+    }
+    __syncthreads();
+    C x[Q];
+    Unroll<0, Q>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        const int slot = s_in[t * Q + j];
+        C v;
+        v.x = 0; v.y = 0;
+        if (slot >= 0 && live) v = a.ring[((long long)slot * 3 + comp) * a.nbins + row];
+        x[j] = v;
+    });
+    fft_dif_reg<C, Q, T>(x, stw, -1, t);
+    Unroll<0, Q>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        sX[t * Q + j][comp][line] = x[j];
+    });
+    __syncthreads();
+    // row `comp` of the symmetric 3x3: components (xx, yy, zz, xy, xz, yz) = 0..5
+    const int i0 = comp == 0 ? 0 : (comp == 1 ? 3 : 4);
+    const int i1 = comp == 0 ? 3 : (comp == 1 ? 1 : 5);
+    const int i2 = comp == 0 ? 4 : (comp == 1 ? 5 : 2);
+    const R sxy = fv ? (R)-1 : (R)1, sxz = fw ? (R)-1 : (R)1, syz = (fv != fw) ? (R)-1 : (R)1;
+    const R s0 = comp == 0 ? (R)1 : (comp == 1 ? sxy : sxz);
+    const R s1 = comp == 0 ? sxy : (comp == 1 ? (R)1 : syz);
+    const R s2 = comp == 0 ? sxz : (comp == 1 ? syz : (R)1);
+    const int brt = bitrev<T>(t);
+    Unroll<0, Q>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        const int w = bitrev<Q>(j) * T + brt;      // frequency of position t Q + j
+        const bool cj = w > S;
+        const int ws = cj ? P - w : w;
+        C y;
+        y.x = 0; y.y = 0;
+        if (live) {
+            const C* hp = a.H + (long long)ws * 6 * a.noct + obin;
+            C h0 = hp[i0 * a.noct], h1 = hp[i1 * a.noct], h2 = hp[i2 * a.noct];
+            if (cj) { h0.y = -h0.y; h1.y = -h1.y; h2.y = -h2.y; }
+            h0.x *= s0; h0.y *= s0; h1.x *= s1; h1.y *= s1; h2.x *= s2; h2.y *= s2;
+            const int pos = t * Q + j;
+            y = cadd(cadd(cmul(h0, sX[pos][0][line]), cmul(h1, sX[pos][1][line])),
+                     cmul(h2, sX[pos][2][line]));
+        }
+        x[j] = y;
+    });
+    fft_dit_reg<C, Q, T>(x, stw, +1, t);
+    if (!live) return;
+    const R scale = (R)1 / (R)P;
+    // outputs are the last S positions: threads t >= T/2 hold them
+    if (t * Q + Q <= S) return;
+    Unroll<0, Q>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        const int pos = t * Q + j;
+        if (pos < S) return;
+        C* dst = a.acc + ((long long)s_out[pos - S] * 3 + comp) * a.nbins + row;
+        const C y = x[j];
+        C v;
+        if (a.overwrite) {
+            v.x = y.x * scale;
+            v.y = y.y * scale;
+        } else {
+            v = *dst;
+            v.x += y.x * scale;
+            v.y += y.y * scale;
+        }
+        *dst = v;
+    });
+}
+
+template <typename R, int Q, int T>
+void far_launch_reg(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
+    constexpr int NB = 32 / T;
+    a.ntile = (c->Hu + NB - 1) / NB;
+    const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
+    k_far_reg<R, Q, T><<<(int)blocks, 96, 0, s>>>(a);
+    MOT_LAUNCH_CHECK();
+}
+
 template <typename R, int TB>
 void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     typedef typename CT<R>::c C;
     a.ntile = (c->Hu + TB - 1) / TB;
     const int P = 2 * a.S;
     const size_t sm = sizeof(C) * ((size_t)P + 2 * (size_t)P * (3 * TB + 1));
-    if (sm > 227 * 1024) throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
+    if (sm > 220 * 1024 || a.S > kMaxLevel)
+        throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
     MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
     k_far<R, TB><<<(int)blocks, NT, sm, s>>>(a);
@@ -391,11 +678,31 @@ void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
     a.tw = twtab<R>(f);
     // lines per CTA: 3 components x TB bins; fewer bins for long levels keeps several
     // CTAs resident per SM
-    const bool fp32 = std::is_same<R, float>::value;
-    if (a.S <= 32) {
-        if (fp32) far_launch<R, 8>(c, a, s); else far_launch<R, 4>(c, a, s);
+    // register-resident lines: up to 32 (FP32) / 16 (FP64) points per thread, a line of
+    // 2S points split over 2S / Q threads (at most 8, 16 (FP64) for S = 128); the
+    // shared-memory kernel beyond
+    if constexpr (std::is_same<R, float>::value) {
+        switch (a.S) {
+            case 2: far_launch_reg<R, 4, 1>(c, a, s); break;
+            case 4: far_launch_reg<R, 8, 1>(c, a, s); break;
+            case 8: far_launch_reg<R, 16, 1>(c, a, s); break;
+            case 16: far_launch_reg<R, 32, 1>(c, a, s); break;
+            case 32: far_launch_reg<R, 32, 2>(c, a, s); break;
+            case 64: far_launch_reg<R, 32, 4>(c, a, s); break;
+            case 128: far_launch_reg<R, 32, 8>(c, a, s); break;
+            default: far_launch<R, 4>(c, a, s);
+        }
     } else {
-        if (fp32) far_launch<R, 4>(c, a, s); else far_launch<R, 2>(c, a, s);
+        switch (a.S) {
+            case 2: far_launch_reg<R, 4, 1>(c, a, s); break;
+            case 4: far_launch_reg<R, 8, 1>(c, a, s); break;
+            case 8: far_launch_reg<R, 16, 1>(c, a, s); break;
+            case 16: far_launch_reg<R, 16, 2>(c, a, s); break;
+            case 32: far_launch_reg<R, 16, 4>(c, a, s); break;
+            case 64: far_launch_reg<R, 16, 8>(c, a, s); break;
+            case 128: far_launch_reg<R, 32, 8>(c, a, s); break;
+            default: far_launch<R, 2>(c, a, s);
+        }
     }
     c->stats.launches += 1;
     c->stats.far_launches += 1;

@@ -100,6 +100,8 @@ struct mot_ctx {
     float* cg32 = nullptr;       // FP32 inner CG vectors r, p, q, e ([4][M] float4)
     int* active = nullptr;       // voxels with chi > 0
     int* nmask = nullptr;        // per active voxel: in-grid neighbours (27 bits)
+    int* tiles = nullptr;        // 8^3 tiles holding active voxels (packed origins)
+    int ntiles = 0;
     float* diag32 = nullptr;     // FP32 copy of cg_diag
     double* vfac = nullptr;      // [4][M]: 0.5/eps, 1/chi (0 if chi = 0), 1/(0.5/eps + d0), chi
     long long nact = 0;

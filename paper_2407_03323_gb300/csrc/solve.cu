@@ -71,6 +71,9 @@ struct CGArgs {
     const int* act;       // active voxels (chi > 0)
     const int* nmask;     // per active voxel: bit e set if neighbour e (0..26) is in the grid
     long long nact;
+    int U, V, W;
+    const int* tiles;     // origins (x | y << 10 | z << 20) of the 8^3 tiles with active voxels
+    int ntiles;
     double* x;            // J_n slot (in/out), SoA [3][M]
     const double* b;      // rhs / chi, SoA
     const float* diag32;  // A's diagonal (T(0)/eps + delta_0)/chi, FP32 copy
@@ -152,6 +155,62 @@ __device__ __forceinline__ float4 applyA32(const CGArgs& a, const float4* __rest
         o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
     }
     return make_float4(o0, o1, o2, 0.f);
+}
+
+// One Chebyshev pass on 8^3 tiles: d_k (with a one-voxel halo, zero outside the grid)
+// is staged in shared memory, then every active voxel of the tile updates
+//   e += d_k, r -= A d_k, d_{k+1} = c1 d_k + c2 r.
+// Inactive voxels (diag = 0) hold zeros in every vector and are skipped.
+constexpr int TT = 8;
+constexpr int TH = TT + 2;
+__device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* __restrict__ dk,
+                                                float4* __restrict__ dn, float c1, float c2) {
+    __shared__ float4 sd[TH * TH * TH];
+    const long long UV = (long long)a.U * a.V;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int org = a.tiles[tile];
+        const int x0 = org & 1023, y0 = (org >> 10) & 1023, z0 = org >> 20;
+        for (int h = threadIdx.x; h < TH * TH * TH; h += blockDim.x) {
+            const int hx = h % TH, hy = (h / TH) % TH, hz = h / (TH * TH);
+            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (x >= 0 && x < a.U && y >= 0 && y < a.V && z >= 0 && z < a.W)
+                v = dk[(long long)z * UV + (long long)y * a.U + x];
+            sd[h] = v;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < TT * TT * TT; q += blockDim.x) {
+            const int lx = q % TT, ly = (q / TT) % TT, lz = q / (TT * TT);
+            const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+            if (x >= a.U || y >= a.V || z >= a.W) continue;
+            const long long m = (long long)z * UV + (long long)y * a.U + x;
+            const float dg = a.diag32[m];
+            if (dg == 0.f) continue;
+            const int hc = ((lz + 1) * TH + (ly + 1)) * TH + (lx + 1);
+            const float* S0 = c_st32 + 13 * 6;
+            const float4 c = sd[hc];
+            float o0 = (dg - S0[0]) * c.x, o1 = (dg - S0[1]) * c.y, o2 = (dg - S0[2]) * c.z;
+#pragma unroll
+            for (int kk = 0; kk < kPairs; ++kk) {
+                const int ep = 14 + kk, em = 12 - kk;
+                const int ex = ep % 3 - 1, ey = (ep / 3) % 3 - 1, ez = ep / 9 - 1;
+                const int off = (ez * TH + ey) * TH + ex;
+                const float4 vp = sd[hc + off], vm = sd[hc - off];
+                const float sx = vp.x + vm.x, sy = vp.y + vm.y, sz = vp.z + vm.z;
+                const float* S = c_st32 + ep * 6;
+                o0 -= S[0] * sx + S[3] * sy + S[4] * sz;
+                o1 -= S[3] * sx + S[1] * sy + S[5] * sz;
+                o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
+            }
+            float4 ev = a.e[m], rv = a.r[m];
+            ev.x += c.x; ev.y += c.y; ev.z += c.z;
+            rv.x -= o0; rv.y -= o1; rv.z -= o2;
+            a.e[m] = ev;
+            a.r[m] = rv;
+            dn[m] = make_float4(c1 * c.x + c2 * rv.x, c1 * c.y + c2 * rv.y, c1 * c.z + c2 * rv.z, 0.f);
+        }
+        __syncthreads();
+    }
 }
 
 // block-wide sum of two values; result valid in every thread
@@ -262,19 +321,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
         float4* dk = a.p;
         float4* dn = a.q;
         for (int k = 0; k < n_it; ++k) {
-            const float c1 = a.c1[k], c2 = a.c2[k];
-            for (long long i = t0; i < a.nact; i += gs) {
-                const int m = a.act[i];
-                const float4 q = applyA32(a, dk, m, a.nmask[i]);
-                const float4 d = dk[m];
-                float4 ev = a.e[m], rv = a.r[m];
-                ev.x += d.x; ev.y += d.y; ev.z += d.z;
-                rv.x -= q.x; rv.y -= q.y; rv.z -= q.z;
-                a.e[m] = ev;
-                a.r[m] = rv;
-                dn[m] = make_float4(c1 * d.x + c2 * rv.x, c1 * d.y + c2 * rv.y,
-                                    c1 * d.z + c2 * rv.z, 0.f);
-            }
+            cheb_pass_tiled(a, dk, dn, a.c1[k], a.c2[k]);
             grid.sync();
             float4* t = dk; dk = dn; dn = t;
         }
@@ -353,31 +400,55 @@ __global__ void k_epilogue_adj(long long M, const double* __restrict__ f,
     const double rhs = g[m * 3 + beta] - P;
     double* Ln = Lring + jslot(s0, 0, jring, st);
     const double chi = f[3 * M + m];
-    if (chi > 0.0) {
-        b[i] = rhs;                                    // A mu = rhs
-        Ln[i] = chi * (3.0 * l1 - 3.0 * l2 + l3);      // start: chi times extrapolated lambda
-    } else {
-        b[i] = 0.0;
-        Ln[i] = rhs * f[2 * M + m];
-    }
+    b[i] = rhs;                                        // A mu = rhs on active voxels
+    // the solve's iterate must vanish off the active set; vacuum voxels get their
+    // lambda after the solve (k_adj_post), when mu is known
+    Ln[i] = chi > 0.0 ? chi * (3.0 * l1 - 3.0 * l2 + l3) : 0.0;
 }
 
-// lambda = mu / chi on active voxels, gradient accumulation
+// lambda = mu / chi on active voxels; on vacuum voxels (chi = 0) the row of Z_0^T reads
+// (T(0) + delta_0) lambda_m - (G_0 * mu)_m = rhs_m, so lambda_m = (rhs_m + (G_0 * mu)_m)
+// / (T(0) + delta_0).  Gradient accumulation on active voxels:
 //   dO/dchi_m += lambda_n,m . (1/chi_m) sum_l (T(l) + delta_l) J_{n-l,m}
 // (the chi-derivative of row m of the forward system, simplified with that row's own
-// equation), and optional AoS output of lambda_n
+// equation), and optional AoS output of lambda_n.  Two launches: the first turns mu
+// into lambda on active voxels only after the second has read mu around vacuum ones.
+__global__ void k_adj_vacuum(long long M, int U, int V, int W, const double* __restrict__ f,
+                             const double* __restrict__ mu, const double* __restrict__ rhs,
+                             double* __restrict__ lam_vac) {
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    if (f[M + m] > 0.0) return;
+    const int u = (int)(m % U), v = (int)((m / U) % V), w = (int)(m / ((long long)U * V));
+    double o[3] = {0.0, 0.0, 0.0};
+    for (int ez = -1; ez <= 1; ++ez)
+        for (int ey = -1; ey <= 1; ++ey)
+            for (int ex = -1; ex <= 1; ++ex) {
+                const int u2 = u + ex, v2 = v + ey, w2 = w + ez;
+                if (u2 < 0 || u2 >= U || v2 < 0 || v2 >= V || w2 < 0 || w2 >= W) continue;
+                const long long m2 = ((long long)w2 * V + v2) * U + u2;
+                const double* S = c_stencil + ((ez + 1) * 9 + (ey + 1) * 3 + (ex + 1)) * 6;
+                const double X = mu[m2], Y = mu[M + m2], Z = mu[2 * M + m2];
+                o[0] += S[0] * X + S[3] * Y + S[4] * Z;
+                o[1] += S[3] * X + S[1] * Y + S[5] * Z;
+                o[2] += S[4] * X + S[5] * Y + S[2] * Z;
+            }
+    for (int beta = 0; beta < 3; ++beta)
+        lam_vac[beta * M + m] = (rhs[beta * M + m] + o[beta]) * f[2 * M + m];
+}
+
 __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __restrict__ Ln,
-                           const double* __restrict__ J, int n, int n_taps,
-                           double* __restrict__ grad_chi, double* __restrict__ lam_out) {
+                           const double* __restrict__ lam_vac, const double* __restrict__ J,
+                           int n, int n_taps, double* __restrict__ grad_chi,
+                           double* __restrict__ lam_out) {
     const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
     const double ichi = f[M + m];
     double gsum = 0.0;
     for (int beta = 0; beta < 3; ++beta) {
-        double lam = Ln[beta * M + m];
+        double lam;
         if (ichi > 0.0) {
-            lam *= ichi;
-            Ln[beta * M + m] = lam;
+            lam = Ln[beta * M + m] * ichi;
             double q = 0.0;
             const int L = n_taps > 2 ? n_taps : 2;
             for (int l = 0; l < L && n - l >= 1; ++l) {
@@ -385,7 +456,10 @@ __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __
                 q += w * J[((long long)(n - l - 1) * M + m) * 3 + beta];
             }
             gsum += lam * q * ichi;
+        } else {
+            lam = lam_vac[beta * M + m];
         }
+        Ln[beta * M + m] = lam;
         if (lam_out) lam_out[m * 3 + beta] = lam;
     }
     grad_chi[m] += gsum;
@@ -634,6 +708,9 @@ CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
     a.act = c->active;
     a.nmask = c->nmask;
     a.nact = c->nact;
+    a.U = c->U; a.V = c->V; a.W = c->W;
+    a.tiles = c->tiles;
+    a.ntiles = c->ntiles;
     a.x = c->J + slot_index(n, c->jring) * 3 * c->M;
     a.b = c->rhs;
     a.diag32 = c->diag32;
@@ -703,10 +780,14 @@ void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double*
     CGArgs a = make_cg_args(c, tau, norm2_out);
     void* args[] = {&a};
     MOT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_cg, c->cg_blocks, NT, args, 0, s));
-    k_adj_post<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(
-        c->M, c->vfac, c->J + (long long)s0 * 3 * c->M, J_aos, n, c->n_taps, grad_chi, lam_out);
+    double* mu = c->J + (long long)s0 * 3 * c->M;
+    k_adj_vacuum<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->U, c->V, c->W, c->vfac, mu,
+                                                           c->rhs, c->cg_q);
     MOT_LAUNCH_CHECK();
-    c->stats.launches += 3;
+    k_adj_post<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->vfac, mu, c->cg_q, J_aos, n,
+                                                         c->n_taps, grad_chi, lam_out);
+    MOT_LAUNCH_CHECK();
+    c->stats.launches += 4;
 }
 
 void write_aos(mot_ctx* c, int n, double* out_dev, cudaStream_t s) {

@@ -257,3 +257,53 @@ def test_blocked_equals_direct_sphere32(mot):
     assert np.linalg.norm(ref) > 0
     assert rel_l2(out[("blocked", "fp64")], ref) < 1e-12
     assert rel_l2(out[("blocked", "fp32_history")], ref) < 1e-5
+
+
+def test_long_grid_levels_to_128(mot):
+    """A 150 x 6 x 5 voxel grid (ell = 152) reaches every far level up to S = 128, whose
+    length-256 temporal lines are split over 8 threads: the GPU table at sampled
+    offsets against the oracle's elements; the blocked history (B = 4, levels 4..128)
+    against the direct sum for a random history of ell steps; and a 300-step blocked
+    march against the direct march (FP64 to rounding, FP32-history to 1e-5)."""
+    from oracle import kernel_table as kt
+    rng = np.random.default_rng(31)
+    eps = 2.0 + 10.0 * rng.uniform(size=(5, 6, 150))
+    eps[2, 3, 40:44] = 1.0
+    taps = wl.fir_taps("hp9", 1e-3)
+    comps = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    with mot.Context(eps, taps) as ctx:
+        ell = ctx.ell
+        assert ell >= 129
+        g = ctx.table(0, ell + 1)
+    for d in [(149, 5, 4), (0, 5, 0), (77, 2, 3), (149, 0, 0), (128, 1, 4)]:
+        vol, face = kt.offset_elements(d, ell + 1)
+        refs = [face[a, b] - (vol if a == b else 0.0) for a, b in comps]
+        scale = max(np.abs(r).max() for r in refs)   # quadrature error ~ largest element
+        for c, ref in enumerate(refs):
+            got = g[:, c, d[2], d[1], d[0]]
+            assert np.abs(got - ref).max() < 1e-12 * scale, (d, c)
+
+    Jh = rng.normal(size=(ell, eps.size, 3))
+    P = {}
+    for scheme, prec in (("direct", "fp64"), ("blocked", "fp64"), ("blocked", "fp32_history")):
+        with mot.Context(eps, taps, precision=prec, scheme=scheme, block=4) as ctx:
+            if scheme == "blocked":
+                assert ctx.levels[-1] == 128
+            P[(scheme, prec)] = ctx.eval_history(Jh)
+    ref = P[("direct", "fp64")]
+    assert rel_l2(P[("blocked", "fp64")], ref) < 1e-12
+    assert rel_l2(P[("blocked", "fp32_history")], ref) < 5e-6
+
+    p = wl.pulse(0, 6.0, k_hat=(1.0, 0.0, 0.0), p_hat=(0.0, 1.0, 0.0))
+    steps = 300
+    out = {}
+    for scheme, prec in (("direct", "fp64"), ("blocked", "fp64"), ("blocked", "fp32_history")):
+        with mot.Context(eps, taps, precision=prec, scheme=scheme, block=4) as ctx:
+            E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 60, 1,
+                               steps)
+            ctx.set_excitation(E)
+            out[(scheme, prec)] = ctx.march(steps)
+    ref = out[("direct", "fp64")]
+    assert np.linalg.norm(ref[-1]) > 1e-3 * np.abs(ref).max()
+    assert rel_l2(out[("blocked", "fp64")], ref) < 1e-12
+    assert rel_l2(out[("blocked", "fp32_history")], ref) < 1e-5
