@@ -115,6 +115,30 @@ mot_status mot_plane_wave(mot_ctx* ctx, const double k_hat[3], const double p_ha
                           double* E_out, void* stream);
 
 /*
+ * mot_plane_wave_static - mot_plane_wave into HOST memory without allocating device
+ * memory.  The paper has no counterpart: this is a library service for callers that
+ * must not allocate during a call (a process whose own pool reserves the device's
+ * memory up front, so a cudaMalloc could fail mid-run; a loop that cannot absorb the
+ * device-wide synchronisation of cudaFree).  mot_plane_wave stages a host result in a
+ * device buffer it allocates per call; this variant stages it in one fixed device
+ * array of 2^21 doubles (16 MiB) per device.
+ *  arguments  as mot_plane_wave; E_out must be host memory ([n_steps][M][3] doubles,
+ *             pageable or pinned), else MOT_ERR_ARG
+ *  limits     3 * M * n_steps <= 2^21, else MOT_ERR_ARG naming both numbers; split
+ *             longer requests over several calls (n_first advances by n_steps)
+ *  set-up     the first call on a device resolves the array's address there (and may
+ *             load the module): make it before any stream capture on that device
+ *  zeroing    none needed: every staged element is written before it is copied out
+ *  races      one array per device per process: calls that overlap in time (several
+ *             host threads, any contexts on the same device) overwrite each other's
+ *             staging data and must be serialised by the caller
+ *  Returns after the result is in E_out (the stream is synchronised).
+ */
+mot_status mot_plane_wave_static(mot_ctx* ctx, const double k_hat[3], const double p_hat[3],
+                                 double f_c, double sigma_t, double t0, int n_first,
+                                 int n_steps, double* E_out, void* stream);
+
+/*
  * mot_march - advance the march by n_steps time steps.
  *  J_out     [n_steps][M][3] doubles receiving J_{n0+1} .. J_{n0+n_steps} (host or
  *            device pointer), or NULL to keep the result on the device only

@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "MOT_OK", 1: "MOT_ERR_ARG", 2: "MOT_ERR_OOM", 3: "MOT_ERR_CUD
 PRECISIONS = {"fp64": 0, "fp32_history": 1}
 SCHEMES = {"direct": 0, "blocked": 1}
 
-EXPORTS = ["mot_create", "mot_destroy", "mot_set_excitation", "mot_plane_wave", "mot_march",
+EXPORTS = ["mot_create", "mot_destroy", "mot_set_excitation", "mot_plane_wave",
+           "mot_plane_wave_static", "mot_march",
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_last_error"]
 
@@ -64,6 +65,7 @@ def load_library(path=LIB_PATH):
     lib.mot_destroy.restype = None
     lib.mot_set_excitation.argtypes = [P, I, P, P]
     lib.mot_plane_wave.argtypes = [P, P, P, D, D, D, I, I, P, P]
+    lib.mot_plane_wave_static.argtypes = [P, P, P, D, D, D, I, I, P, P]
     lib.mot_march.argtypes = [P, I, P, P]
     lib.mot_eval_history.argtypes = [P, I, P, P, P]
     lib.mot_adjoint.argtypes = [P, I, P, P, P, P, P]
@@ -180,6 +182,19 @@ class Context:
         p = np.ascontiguousarray(p_hat, dtype=np.float64)
         self._check(self._lib.mot_plane_wave(self._h, k.ctypes.data, p.ctypes.data, f_c, sigma_t,
                                              t0, n_first, n_steps, _ptr(out), _stream(stream)))
+        return out
+
+    def plane_wave_static(self, k_hat, p_hat, f_c, sigma_t, t0, n_first, n_steps, out=None,
+                          stream=None):
+        """mot_plane_wave_static: as plane_wave, into host memory (numpy), staged in
+        the library's fixed device scratch instead of a per-call allocation."""
+        if out is None:
+            out = np.zeros((n_steps, self.M, 3))
+        k = np.ascontiguousarray(k_hat, dtype=np.float64)
+        p = np.ascontiguousarray(p_hat, dtype=np.float64)
+        self._check(self._lib.mot_plane_wave_static(self._h, k.ctypes.data, p.ctypes.data, f_c,
+                                                    sigma_t, t0, n_first, n_steps, _ptr(out),
+                                                    _stream(stream)))
         return out
 
     def march(self, n_steps, out="host", stream=None):
