@@ -66,6 +66,12 @@ struct MacGeom {
     long long nbins, noct;
 };
 
+// this step's entries of the far levels' accumulator rings ([3][nbins] each)
+template <typename C> struct FarSums {
+    const C* p[8];
+    int n;
+};
+
 // Phat(k) = scale * sum_{l=1}^{L} Ghat_l(k) Jhat_{n-l}(k) over all rfft bins.
 // A warp covers 8 consecutive octant bins (ku) x 4 mirrors: lane = mirror * 8 + j.
 // The 8 lanes of a mirror read 8 consecutive bins of a ring row; the kernel values of
@@ -76,7 +82,7 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
                                             const typename CT<R>::c* __restrict__ ring, int hring,
                                             int slot_first, int L, MacGeom g, R scale,
                                             typename CT<R>::c* __restrict__ phat,
-                                            typename CT<R>::c* __restrict__ acc) {
+                                            FarSums<typename CT<R>::c> far) {
     typedef typename CT<R>::c C;
     typedef typename std::conditional<std::is_same<R, double>::value, double2, float2>::type R2;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -98,10 +104,11 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
     const R syz = (fv != fw) ? (R)-1 : (R)1;
     Acc<R> ax, ay, az;
     ax.zero(); ay.zero(); az.zero();
-    if (acc) {   // far-lag contributions of this step (the top level rewrites the slot)
-        ax.add(acc[bidx]);
-        ay.add(acc[g.nbins + bidx]);
-        az.add(acc[2 * g.nbins + bidx]);
+    for (int k = 0; k < far.n; ++k) {   // far-lag contributions of this step
+        const C* f = far.p[k];
+        ax.add(f[bidx]);
+        ay.add(f[g.nbins + bidx]);
+        az.add(f[2 * g.nbins + bidx]);
     }
     const long long slot_stride = 3 * g.nbins;
     int slot = slot_first;
@@ -173,17 +180,16 @@ template <typename R> struct FarArgs {
     int hring;
     long long nbins, noct;
     const C* H;          // level spectra [S+1][6][noct]
-    C* acc;              // [smax][3][nbins]
-    int smax;
+    C* acc;              // this level's accumulator ring [smax][3][nbins]
+    int smax;            // its length (S)
     int n0, S, lmax;
     int Hu, Hv, Hw, Pv, Pw;
     int ntile;
-    int overwrite;       // 1: first writer of these accumulators (top level)
     RadixList rl;        // length 2S
     const C* tw;
 };
 
-// one level firing at step n0: adds y(n0 + j), j < S, into the accumulator ring
+// one level firing at step n0: writes y(n0 + j), j < S, to the level's accumulator ring
 template <typename R, int TB>
 __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
     typedef typename CT<R>::c C;
@@ -269,14 +275,8 @@ __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
         C* dst = a.acc + (slot * 3 + comp) * a.nbins + row + bb;
         const C y = Y[(a.S + j) * ld + t];
         C v;
-        if (a.overwrite) {
-            v.x = y.x * scale;
-            v.y = y.y * scale;
-        } else {
-            v = *dst;
-            v.x += y.x * scale;
-            v.y += y.y * scale;
-        }
+        v.x = y.x * scale;
+        v.y = y.y * scale;
         *dst = v;
     }
 }
@@ -315,7 +315,14 @@ void history_alloc(mot_ctx* c) {
             fft_plan_axis(c->lev_fft[c->nlev], 2 * S);
             ++c->nlev;
         }
-        c->smax = c->nlev ? c->lev_S[c->nlev - 1] : 1;
+        // one accumulator ring per level (S slots each): every firing writes its
+        // outputs, the near MAC of a step sums the levels' entries for that step
+        long long acc_slots = 0;
+        for (int k = 0; k < c->nlev; ++k) {
+            c->lev_acc[k] = acc_slots;
+            acc_slots += c->lev_S[k];
+        }
+        c->smax = std::max<long long>(acc_slots, 1);
         if (c->nlev && 2 * c->lev_S[c->nlev - 1] < c->ell + 1)
             throw MotError{MOT_ERR_ARG, "blocked scheme: more than 8 levels needed; raise block"};
         MOT_CUDA_TRY(cudaMalloc(&hb.level_spec, sizeof(C) * std::max<long long>(spec, 1)));
@@ -390,44 +397,96 @@ template <int E> struct Unroll<E, E> {
     template <typename F> __device__ __forceinline__ static void run(F&&) {}
 };
 
+// Twiddles known at compile time: cos and sin of 2 pi k / n by the Taylor series of
+// sin and cos on [0, pi/4], after reducing the angle with the quadrant and octant
+// symmetries in exact integer arithmetic.  Evaluated only by the compiler (constexpr
+// initialisers), so the radix-2 stages below multiply by literal constants.
+struct CTw { double re, im; };
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int i = 1; i < 14; ++i) {
+        term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i < 14; ++i) {
+        term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        sum += term;
+    }
+    return sum;
+}
+// exp(-2 pi i k / n), 0 <= k < n
+__host__ __device__ constexpr CTw root_of_unity(int k, int n) {
+    constexpr double pi = 3.141592653589793238462643383279502884;
+    const int q = (4 * k) / n;               // quadrant of 2 pi k / n
+    const int r = 4 * k - q * n;             // remainder angle = (pi / 2) r / n, r in [0, n)
+    const bool hi = 2 * r > n;               // beyond pi / 4: use the complement
+    const double phi = (pi / 2.0) * (double)(hi ? n - r : r) / (double)n;
+    const double c0 = hi ? taylor_sin(phi) : taylor_cos(phi);
+    const double s0 = hi ? taylor_cos(phi) : taylor_sin(phi);
+    // angle = q pi/2 + (pi/2) r / n ; (cos, sin) of it
+    const double ca = q == 0 ? c0 : (q == 1 ? -s0 : (q == 2 ? -c0 : s0));
+    const double sa = q == 0 ? s0 : (q == 1 ? c0 : (q == 2 ? -s0 : -c0));
+    return CTw{ca, -sa};
+}
+static_assert(root_of_unity(0, 8).re == 1.0 && root_of_unity(2, 8).im == -1.0, "twiddle");
+static_assert(root_of_unity(4, 8).re == -1.0 && root_of_unity(6, 8).im == 1.0, "twiddle");
+static_assert(root_of_unity(1, 6).re - 0.5 < 1e-16 && 0.5 - root_of_unity(1, 6).re < 1e-16,
+              "twiddle");
+static_assert(root_of_unity(1, 8).re - 0.70710678118654752 < 2e-16 &&
+              0.70710678118654752 - root_of_unity(1, 8).re < 2e-16, "twiddle");
+
+// v * W_N^K for compile-time K, N; DIR = -1 forward (W = exp(-2 pi i / N)), +1 inverse
+template <int K, int N, int DIR, typename C>
+__device__ __forceinline__ C twiddle_c(C v) {
+    typedef decltype(v.x) R;
+    if constexpr (K == 0) {
+        return v;
+    } else if constexpr (4 * K == N) {        // -i (forward) / +i (inverse)
+        C o;
+        if (DIR < 0) { o.x = v.y; o.y = -v.x; } else { o.x = -v.y; o.y = v.x; }
+        return o;
+    } else {
+        constexpr CTw w = root_of_unity(K, N);
+        constexpr R wr = (R)w.re;
+        constexpr R wi = (R)(DIR < 0 ? w.im : -w.im);
+        C o;
+        o.x = v.x * wr - v.y * wi;
+        o.y = v.x * wi + v.y * wr;
+        return o;
+    }
+}
+
 // Lines of length P = T * Q are split over T threads; thread t holds positions
 // t Q .. t Q + Q - 1 of the (natural- or bit-reversed-order) line.  Stages whose span
 // reaches across threads exchange values with the partner thread by warp shuffles
-// (lane = t * (32 / T) + line); the others are register-local.  Twiddles index the
-// table of P roots with the stage's stride.
+// (lane = t * (32 / T) + line) and take their twiddles from a shared table of the P
+// roots; the others are register-local with literal twiddles.
 
 // local DIF stage of span LEN (<= Q) over the thread's Q values
-template <typename C, int Q, int P, int LEN>
-__device__ __forceinline__ void dif_local(C* x, const C* __restrict__ tw, int dir) {
-    constexpr int half = LEN / 2, ts = P / LEN;
+template <typename C, int Q, int LEN, int DIR>
+__device__ __forceinline__ void dif_local(C* x) {
+    constexpr int half = LEN / 2;
     Unroll<0, Q / 2>::run([&](auto q) {
         constexpr int st = (decltype(q)::value / half) * LEN;
         constexpr int k = decltype(q)::value % half;
         const C a = x[st + k], b = x[st + k + half];
         x[st + k] = cadd(a, b);
-        C d = csub(a, b);
-        if (k) {
-            C w = tw[k * ts];
-            if (dir > 0) w.y = -w.y;
-            d = cmul(d, w);
-        }
-        x[st + k + half] = d;
+        x[st + k + half] = twiddle_c<k, LEN, DIR>(csub(a, b));
     });
 }
 
-template <typename C, int Q, int P, int LEN>
-__device__ __forceinline__ void dit_local(C* x, const C* __restrict__ tw, int dir) {
-    constexpr int half = LEN / 2, ts = P / LEN;
+template <typename C, int Q, int LEN, int DIR>
+__device__ __forceinline__ void dit_local(C* x) {
+    constexpr int half = LEN / 2;
     Unroll<0, Q / 2>::run([&](auto q) {
         constexpr int st = (decltype(q)::value / half) * LEN;
         constexpr int k = decltype(q)::value % half;
         const C a = x[st + k];
-        C b = x[st + k + half];
-        if (k) {
-            C w = tw[k * ts];
-            if (dir > 0) w.y = -w.y;
-            b = cmul(b, w);
-        }
+        const C b = twiddle_c<k, LEN, DIR>(x[st + k + half]);
         x[st + k] = cadd(a, b);
         x[st + k + half] = csub(a, b);
     });
@@ -444,9 +503,15 @@ __device__ __forceinline__ double2 shfl_c(double2 v, int mask) {
     return v;
 }
 
+template <int DIR, typename C> __device__ __forceinline__ C table_tw(const C* tw, int i) {
+    C w = tw[i];
+    if (DIR > 0) w.y = -w.y;
+    return w;
+}
+
 // cross-thread DIF stage: span LEN = 2 * HT * Q, partner thread t ^ HT
-template <typename C, int Q, int T, int HT>
-__device__ __forceinline__ void dif_cross(C* x, const C* __restrict__ tw, int dir, int t) {
+template <typename C, int Q, int T, int HT, int DIR>
+__device__ __forceinline__ void dif_cross(C* x, const C* __restrict__ tw, int t) {
     constexpr int P = Q * T, LEN = 2 * HT * Q, ts = P / LEN;
     const bool upper = (t & HT) == 0;
     const int base = ((t & ~HT) * Q) % LEN;
@@ -454,92 +519,112 @@ __device__ __forceinline__ void dif_cross(C* x, const C* __restrict__ tw, int di
         constexpr int j = decltype(q)::value;
         const C mine = x[j];
         const C other = shfl_c(mine, HT * (32 / T));
-        if (upper) {
-            x[j] = cadd(mine, other);
-        } else {
-            C w = tw[(base + j) * ts];
-            if (dir > 0) w.y = -w.y;
-            x[j] = cmul(csub(other, mine), w);
-        }
+        if (upper) x[j] = cadd(mine, other);
+        else x[j] = cmul(csub(other, mine), table_tw<DIR>(tw, (base + j) * ts));
     });
 }
 
-template <typename C, int Q, int T, int HT>
-__device__ __forceinline__ void dit_cross(C* x, const C* __restrict__ tw, int dir, int t) {
+template <typename C, int Q, int T, int HT, int DIR>
+__device__ __forceinline__ void dit_cross(C* x, const C* __restrict__ tw, int t) {
     constexpr int P = Q * T, LEN = 2 * HT * Q, ts = P / LEN;
     const bool upper = (t & HT) == 0;
     const int base = ((t & ~HT) * Q) % LEN;
     Unroll<0, Q>::run([&](auto q) {
         constexpr int j = decltype(q)::value;
         C send = x[j];
-        if (!upper) {
-            C w = tw[(base + j) * ts];
-            if (dir > 0) w.y = -w.y;
-            send = cmul(send, w);
-        }
+        if (!upper) send = cmul(send, table_tw<DIR>(tw, (base + j) * ts));
         const C recv = shfl_c(send, HT * (32 / T));
         x[j] = upper ? cadd(send, recv) : csub(recv, send);
     });
 }
 
-template <typename C, int Q, int T, int LEN> struct DifLoc {
-    __device__ __forceinline__ static void run(C* x, const C* tw, int dir) {
-        dif_local<C, Q, Q * T, LEN>(x, tw, dir);
-        DifLoc<C, Q, T, LEN / 2>::run(x, tw, dir);
+template <typename C, int Q, int T, int LEN, int DIR> struct DifLoc {
+    __device__ __forceinline__ static void run(C* x) {
+        dif_local<C, Q, LEN, DIR>(x);
+        DifLoc<C, Q, T, LEN / 2, DIR>::run(x);
     }
 };
-template <typename C, int Q, int T> struct DifLoc<C, Q, T, 1> {
+template <typename C, int Q, int T, int DIR> struct DifLoc<C, Q, T, 1, DIR> {
+    __device__ __forceinline__ static void run(C*) {}
+};
+template <typename C, int Q, int T, int LEN, int DIR> struct DitLoc {
+    __device__ __forceinline__ static void run(C* x) {
+        dit_local<C, Q, LEN, DIR>(x);
+        DitLoc<C, Q, T, LEN * 2, DIR>::run(x);
+    }
+};
+template <typename C, int Q, int T, int DIR> struct DitLoc<C, Q, T, 2 * Q, DIR> {
+    __device__ __forceinline__ static void run(C*) {}
+};
+template <typename C, int Q, int T, int HT, int DIR> struct DifCross {
+    __device__ __forceinline__ static void run(C* x, const C* tw, int t) {
+        dif_cross<C, Q, T, HT, DIR>(x, tw, t);
+        DifCross<C, Q, T, HT / 2, DIR>::run(x, tw, t);
+    }
+};
+template <typename C, int Q, int T, int DIR> struct DifCross<C, Q, T, 0, DIR> {
     __device__ __forceinline__ static void run(C*, const C*, int) {}
 };
-template <typename C, int Q, int T, int LEN> struct DitLoc {
-    __device__ __forceinline__ static void run(C* x, const C* tw, int dir) {
-        dit_local<C, Q, Q * T, LEN>(x, tw, dir);
-        DitLoc<C, Q, T, LEN * 2>::run(x, tw, dir);
+template <typename C, int Q, int T, int HT, int DIR> struct DitCross {
+    __device__ __forceinline__ static void run(C* x, const C* tw, int t) {
+        dit_cross<C, Q, T, HT, DIR>(x, tw, t);
+        DitCross<C, Q, T, HT * 2, DIR>::run(x, tw, t);
     }
 };
-template <typename C, int Q, int T> struct DitLoc<C, Q, T, 2 * Q> {
+template <typename C, int Q, int T, int DIR> struct DitCross<C, Q, T, T, DIR> {
     __device__ __forceinline__ static void run(C*, const C*, int) {}
-};
-template <typename C, int Q, int T, int HT> struct DifCross {
-    __device__ __forceinline__ static void run(C* x, const C* tw, int dir, int t) {
-        dif_cross<C, Q, T, HT>(x, tw, dir, t);
-        DifCross<C, Q, T, HT / 2>::run(x, tw, dir, t);
-    }
-};
-template <typename C, int Q, int T> struct DifCross<C, Q, T, 0> {
-    __device__ __forceinline__ static void run(C*, const C*, int, int) {}
-};
-template <typename C, int Q, int T, int HT> struct DitCross {
-    __device__ __forceinline__ static void run(C* x, const C* tw, int dir, int t) {
-        dit_cross<C, Q, T, HT>(x, tw, dir, t);
-        DitCross<C, Q, T, HT * 2>::run(x, tw, dir, t);
-    }
-};
-template <typename C, int Q, int T> struct DitCross<C, Q, T, T> {
-    __device__ __forceinline__ static void run(C*, const C*, int, int) {}
 };
 
 // natural order in, bit-reversed out: cross stages (span > Q) first, then local
-template <typename C, int Q, int T>
-__device__ __forceinline__ void fft_dif_reg(C* x, const C* __restrict__ tw, int dir, int t) {
-    DifCross<C, Q, T, T / 2>::run(x, tw, dir, t);
-    DifLoc<C, Q, T, Q>::run(x, tw, dir);
+template <typename C, int Q, int T, int DIR>
+__device__ __forceinline__ void fft_dif_reg(C* x, const C* __restrict__ tw, int t) {
+    DifCross<C, Q, T, T / 2, DIR>::run(x, tw, t);
+    DifLoc<C, Q, T, Q, DIR>::run(x);
 }
 // bit-reversed in, natural order out: local stages first, then cross
-template <typename C, int Q, int T>
-__device__ __forceinline__ void fft_dit_reg(C* x, const C* __restrict__ tw, int dir, int t) {
-    DitLoc<C, Q, T, 2>::run(x, tw, dir);
-    DitCross<C, Q, T, 1>::run(x, tw, dir, t);
+template <typename C, int Q, int T, int DIR>
+__device__ __forceinline__ void fft_dit_reg(C* x, const C* __restrict__ tw, int t) {
+    DitLoc<C, Q, T, 2, DIR>::run(x);
+    DitCross<C, Q, T, 1, DIR>::run(x, tw, t);
 }
 
+// asynchronous global -> shared copy of one complex value (8 or 16 bytes)
+template <typename C>
+__device__ __forceinline__ void cp_async_c(C* dst, const C* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <typename R, int Q, int T> struct FarRegSmem {
+    typedef typename CT<R>::c C;
+    static constexpr int P = Q * T, S = P / 2, NB = 32 / T;
+    C X[P][3][NB];          // forward spectra of the three components
+    C H[S + 1][6][NB];      // the block's level spectra, w = 0..S
+    C tw[P];                // roots of unity for the cross-thread stages
+    int in[P];              // ring slot of every window time (-1: none)
+    int out[S];             // accumulator slot of every output time
+};
+
+// One level firing at step n0: y(n0 + j), j < S, written to the level's accumulator
+// ring.  Block = three warps (warp = component) over 32 / T bins of one rfft row.
+// The block's kernel spectra are copied to shared memory asynchronously while the
+// window is loaded and transformed.  Mirror signs: the off-diagonal spectra of the
+// mirrored rows flip as s_ab = sigma_a sigma_b (sigma_x = 1, sigma_y = -1 if v is
+// mirrored, sigma_z = -1 if w is), so the product uses the octant spectra on
+// sigma-scaled inputs and scales each output row by its sigma.
 template <typename R, int Q, int T>
 __global__ void __launch_bounds__(96) k_far_reg(FarArgs<R> a) {
     typedef typename CT<R>::c C;
-    constexpr int P = Q * T, S = P / 2, NB = 32 / T;   // NB bins per warp
-    __shared__ C sX[P][3][NB];
-    __shared__ C stw[P];
-    __shared__ int s_in[P];
-    __shared__ int s_out[S];
+    typedef FarRegSmem<R, Q, T> SM;
+    constexpr int P = SM::P, S = SM::S, NB = SM::NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SM& sm = *reinterpret_cast<SM*>(smem_raw);
     const int comp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int t = lane / NB, line = lane % NB;
     const int ut = blockIdx.x % a.ntile;
@@ -553,90 +638,83 @@ __global__ void __launch_bounds__(96) k_far_reg(FarArgs<R> a) {
     if ((fv && !mv) || (fw && !mw)) return;
     const int kv = fv ? a.Pv - kv_o : kv_o;
     const int kw = fw ? a.Pw - kw_o : kw_o;
-    const int ku = ut * NB + line;
-    const bool live = ku < a.Hu;
-    const long long row = ((long long)kw * a.Pv + kv) * a.Hu + ku;
-    const long long obin = ((long long)kw_o * a.Hv + kv_o) * a.Hu + ku;
+    const int ku0 = ut * NB;
+    const int nlive = min(NB, a.Hu - ku0);
+    const bool live = line < nlive;
+    const long long row = ((long long)kw * a.Pv + kv) * a.Hu + ku0 + line;
+    const long long obase = ((long long)kw_o * a.Hv + kv_o) * a.Hu + ku0;
+    for (int i = threadIdx.x; i < (S + 1) * 6 * NB; i += blockDim.x) {
+        const int l = i % NB;
+        if (l < nlive) cp_async_c(&sm.H[0][0][0] + i, a.H + (long long)(i / NB) * a.noct + obase + l);
+    }
     const int tfirst = max(1, a.n0 - a.lmax);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int time = a.n0 - P + i;
-        s_in[i] = time >= tfirst ? time % a.hring : -1;
-        stw[i] = a.tw[i];
-        if (i < S) s_out[i] = (a.n0 + i) % a.smax;
+        sm.in[i] = time >= tfirst ? time % a.hring : -1;
+        sm.tw[i] = a.tw[i];
+        if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
     }
     __syncthreads();
+    const R sig = comp == 0 ? (R)1 : (comp == 1 ? (fv ? (R)-1 : (R)1) : (fw ? (R)-1 : (R)1));
     C x[Q];
     Unroll<0, Q>::run([&](auto q) {
         constexpr int j = decltype(q)::value;
-        const int slot = s_in[t * Q + j];
+        const int slot = sm.in[t * Q + j];
         C v;
         v.x = 0; v.y = 0;
         if (slot >= 0 && live) v = a.ring[((long long)slot * 3 + comp) * a.nbins + row];
         x[j] = v;
     });
-    fft_dif_reg<C, Q, T>(x, stw, -1, t);
+    fft_dif_reg<C, Q, T, -1>(x, sm.tw, t);
     Unroll<0, Q>::run([&](auto q) {
         constexpr int j = decltype(q)::value;
-        sX[t * Q + j][comp][line] = x[j];
+        C v = x[j];
+        v.x *= sig; v.y *= sig;
+        sm.X[t * Q + j][comp][line] = v;
     });
+    cp_async_commit_wait();
     __syncthreads();
     // row `comp` of the symmetric 3x3: components (xx, yy, zz, xy, xz, yz) = 0..5
     const int i0 = comp == 0 ? 0 : (comp == 1 ? 3 : 4);
     const int i1 = comp == 0 ? 3 : (comp == 1 ? 1 : 5);
     const int i2 = comp == 0 ? 4 : (comp == 1 ? 5 : 2);
-    const R sxy = fv ? (R)-1 : (R)1, sxz = fw ? (R)-1 : (R)1, syz = (fv != fw) ? (R)-1 : (R)1;
-    const R s0 = comp == 0 ? (R)1 : (comp == 1 ? sxy : sxz);
-    const R s1 = comp == 0 ? sxy : (comp == 1 ? (R)1 : syz);
-    const R s2 = comp == 0 ? sxz : (comp == 1 ? syz : (R)1);
     const int brt = bitrev<T>(t);
     Unroll<0, Q>::run([&](auto q) {
         constexpr int j = decltype(q)::value;
         const int w = bitrev<Q>(j) * T + brt;      // frequency of position t Q + j
         const bool cj = w > S;
         const int ws = cj ? P - w : w;
-        C y;
-        y.x = 0; y.y = 0;
-        if (live) {
-            const C* hp = a.H + (long long)ws * 6 * a.noct + obin;
-            C h0 = hp[i0 * a.noct], h1 = hp[i1 * a.noct], h2 = hp[i2 * a.noct];
-            if (cj) { h0.y = -h0.y; h1.y = -h1.y; h2.y = -h2.y; }
-            h0.x *= s0; h0.y *= s0; h1.x *= s1; h1.y *= s1; h2.x *= s2; h2.y *= s2;
-            const int pos = t * Q + j;
-            y = cadd(cadd(cmul(h0, sX[pos][0][line]), cmul(h1, sX[pos][1][line])),
-                     cmul(h2, sX[pos][2][line]));
-        }
-        x[j] = y;
+        C h0 = sm.H[ws][i0][line], h1 = sm.H[ws][i1][line], h2 = sm.H[ws][i2][line];
+        if (cj) { h0.y = -h0.y; h1.y = -h1.y; h2.y = -h2.y; }
+        const int pos = t * Q + j;
+        x[j] = cadd(cadd(cmul(h0, sm.X[pos][0][line]), cmul(h1, sm.X[pos][1][line])),
+                    cmul(h2, sm.X[pos][2][line]));
     });
-    fft_dit_reg<C, Q, T>(x, stw, +1, t);
+    fft_dit_reg<C, Q, T, +1>(x, sm.tw, t);
     if (!live) return;
-    const R scale = (R)1 / (R)P;
+    const R scale = sig / (R)P;
     // outputs are the last S positions: threads t >= T/2 hold them
     if (t * Q + Q <= S) return;
     Unroll<0, Q>::run([&](auto q) {
         constexpr int j = decltype(q)::value;
         const int pos = t * Q + j;
         if (pos < S) return;
-        C* dst = a.acc + ((long long)s_out[pos - S] * 3 + comp) * a.nbins + row;
-        const C y = x[j];
-        C v;
-        if (a.overwrite) {
-            v.x = y.x * scale;
-            v.y = y.y * scale;
-        } else {
-            v = *dst;
-            v.x += y.x * scale;
-            v.y += y.y * scale;
-        }
-        *dst = v;
+        C v = x[j];
+        v.x *= scale; v.y *= scale;
+        a.acc[((long long)sm.out[pos - S] * 3 + comp) * a.nbins + row] = v;
     });
 }
 
 template <typename R, int Q, int T>
 void far_launch_reg(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
-    constexpr int NB = 32 / T;
-    a.ntile = (c->Hu + NB - 1) / NB;
+    typedef FarRegSmem<R, Q, T> SM;
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far_reg<R, Q, T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SM)));
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far_reg<R, Q, T>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    a.ntile = (c->Hu + SM::NB - 1) / SM::NB;
     const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
-    k_far_reg<R, Q, T><<<(int)blocks, 96, 0, s>>>(a);
+    k_far_reg<R, Q, T><<<(int)blocks, 96, sizeof(SM), s>>>(a);
     MOT_LAUNCH_CHECK();
 }
 
@@ -663,14 +741,13 @@ void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
     a.nbins = c->nbins;
     a.noct = c->noct;
     a.H = hb.level_spec + c->lev_off[k];
-    a.acc = hb.acc_ring;
-    a.smax = c->smax;
+    a.acc = hb.acc_ring + c->lev_acc[k] * 3 * c->nbins;
+    a.smax = c->lev_S[k];
     a.n0 = n0;
     a.S = c->lev_S[k];
     a.lmax = std::min(2 * a.S - 1, c->ell);
     a.Hu = c->Hu; a.Hv = c->Hv; a.Hw = c->Hw;
     a.Pv = c->ax[1].P; a.Pw = c->ax[2].P;
-    a.overwrite = (k == c->nlev - 1) ? 1 : 0;
     const AxisFFT& f = c->lev_fft[k];
     a.rl.P = f.P;
     a.rl.n = f.nrad;
@@ -722,17 +799,20 @@ void history_step(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t* ev) {
     }
     if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
     const bool blocked = c->scheme == MOT_HISTORY_BLOCKED;
-    if (blocked)   // largest level first: it writes the accumulators, the others add
+    if (blocked)   // each firing level writes its own accumulator ring
         for (int k = c->nlev - 1; k >= 0; --k)
             if ((n - 1) % c->lev_S[k] == 0) far_level<R>(c, k, n, s);
     if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[1], s));
     const R scale = (R)(1.0 / ((double)c->ax[0].P * c->ax[1].P * c->ax[2].P));
     const long long nblk = (c->noct + 8 * (NT / 32) - 1) / (8 * (NT / 32));
     const int L = blocked ? std::min(c->block - 1, c->ell) : c->ell;
-    C* acc = blocked ? hb.acc_ring + slot_index(n, c->smax) * slot : nullptr;
+    FarSums<C> far;
+    far.n = blocked ? c->nlev : 0;
+    for (int k = 0; k < far.n; ++k)
+        far.p[k] = hb.acc_ring + (c->lev_acc[k] + slot_index(n, c->lev_S[k])) * slot;
     k_mac<R><<<(int)nblk, NT, 0, s>>>(hb.ghat, hb.jhat_ring, c->hring,
                                       (int)slot_index(n - 1, c->hring), L, geom(c), scale,
-                                      hb.phat, acc);
+                                      hb.phat, far);
     MOT_LAUNCH_CHECK();
     c->stats.launches += 1;
     c->stats.mac_launches += 1;

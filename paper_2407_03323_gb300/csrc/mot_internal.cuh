@@ -64,7 +64,7 @@ template <typename R> struct HistoryBuffers {
     C* tmp2 = nullptr;
     R* hist_spatial = nullptr;   // [3][W][V][U]   (G * J history, spatial)
     // blocked temporal scheme
-    C* acc_ring = nullptr;       // [S_max][3][Pw][Pv][Hu] future far-lag sums
+    C* acc_ring = nullptr;       // per level [S][3][Pw][Pv][Hu] future far-lag sums
     C* level_spec = nullptr;     // per level kernel temporal spectra (octant)
 };
 
@@ -135,7 +135,8 @@ struct mot_ctx {
     int lev_S[8] = {0};
     long long lev_off[8] = {0};  // offsets of the level spectra
     AxisFFT lev_fft[8];          // temporal FFT plans of length 2S
-    int smax = 1;                // accumulator ring length (largest S)
+    long long lev_acc[8] = {0};  // first accumulator slot of each level's ring
+    long long smax = 1;          // accumulator slots of all levels (sum of S)
 
     bool adjoint = false;        // rings hold lambda; the FFT input is chi * lambda
 

