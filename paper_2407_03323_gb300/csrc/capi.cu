@@ -62,12 +62,13 @@ void free_all(mot_ctx* c) {
     for (int k = 0; k < 8; ++k) mot::fft_free_axis(c->lev_fft[k]);
     mot::history_free<double>(c);
     mot::history_free<float>(c);
-    double* dptrs[] = {c->eps, c->chi, c->cg_diag, c->J, c->rhs, c->cg_r, c->cg_p,
+    double* dptrs[] = {c->eps, c->chi, c->cg_diag, c->J, c->rhs, c->cg_r,
                        c->cg_q, c->red, c->norms, c->outbuf, c->tab, c->Estage};
     for (double* p : dptrs) cudaFree(p);
     cudaFree(c->tab_l0);
     cudaFree(c->dstatus);
     cudaFree(c->cg32);
+    cudaFree(c->cg_df);
     cudaFree(c->active);
     cudaFree(c->nmask);
     cudaFree(c->tiles);
@@ -192,7 +193,6 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         MOT_CUDA_TRY(cudaMalloc(&c->J, sizeof(double) * 3 * M * c->jring));
         MOT_CUDA_TRY(cudaMalloc(&c->rhs, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg_r, sizeof(double) * 3 * M));
-        MOT_CUDA_TRY(cudaMalloc(&c->cg_p, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg_q, sizeof(double) * 3 * M));
         MOT_CUDA_TRY(cudaMalloc(&c->cg32, sizeof(float) * 16 * M));
         MOT_CUDA_TRY(cudaMemset(c->cg32, 0, sizeof(float) * 16 * M));
@@ -253,6 +253,16 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
             MOT_CUDA_TRY(cudaMalloc(&c->diag32, sizeof(float) * M));
             MOT_CUDA_TRY(cudaMalloc(&c->vfac, sizeof(double) * 4 * M));
             MOT_CUDA_TRY(cudaMemcpy(c->diag32, d32.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
+            if (precision == MOT_FP32_HISTORY) {
+                // float-pair state of the double-float residual; entries of inactive
+                // voxels stay zero (neighbours read them)
+                MOT_CUDA_TRY(cudaMalloc(&c->cg_df, sizeof(float) * 17 * M));
+                MOT_CUDA_TRY(cudaMemset(c->cg_df, 0, sizeof(float) * 16 * M));
+                std::vector<float> dlo(M);
+                for (long long m = 0; m < M; ++m) dlo[m] = (float)(dg[m] - (double)d32[m]);
+                MOT_CUDA_TRY(cudaMemcpy(c->cg_df + 16 * M, dlo.data(), sizeof(float) * M,
+                                        cudaMemcpyHostToDevice));
+            }
             MOT_CUDA_TRY(cudaMemcpy(c->vfac, vf.data(), sizeof(double) * 4 * M, cudaMemcpyHostToDevice));
         }
         MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));

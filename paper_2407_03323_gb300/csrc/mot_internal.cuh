@@ -95,7 +95,7 @@ struct mot_ctx {
     double* J = nullptr;         // spatial J ring [jring][3][M] (SoA per slot)
     double* rhs = nullptr;       // [3][M]
     double* cg_r = nullptr;
-    double* cg_p = nullptr;
+    float* cg_df = nullptr;      // FP32-history: x, b as float pairs ([4][M] float4), diag low parts [M]
     double* cg_q = nullptr;
     float* cg32 = nullptr;       // FP32 inner CG vectors r, p, q, e ([4][M] float4)
     int* active = nullptr;       // voxels with chi > 0

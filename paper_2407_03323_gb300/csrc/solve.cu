@@ -85,6 +85,13 @@ struct CGArgs {
     float4* p;
     float4* q;
     float4* e;
+    // double-float residual state (FP32-history): x and b as float pairs hi + lo, and
+    // the low parts of the diagonal (its high parts are diag32)
+    float4* xh;
+    float4* xl;
+    float4* bh;
+    float4* bl;
+    const float* diag_lo;
     double* red;          // [3][gridDim]
     double tol2;          // outer tolerance^2 (relative to ||b||^2)
     float inv_theta;      // Chebyshev: 1 / theta, theta = (lmin + lmax) / 2
@@ -102,6 +109,7 @@ struct CGArgs {
 // neighbour e = (ez+1)*9 + (ey+1)*3 + (ex+1); c_noff[e] = ex + U ey + U V ez
 __constant__ int c_noff[27];
 __constant__ float c_st32[27 * 6];   // FP32 copy of c_stencil
+__constant__ float c_stl[27 * 6];    // c_stencil - c_st32 rounded to FP32 (double-float low parts)
 // the 13 neighbours e > 13 pair with their mirrors 26 - e; G_0(-e) = G_0(e)
 
 // Neighbour pair EP, 26 - EP of the 27-point stencil (G_0(-e) = G_0(e), so the pair's
@@ -161,6 +169,121 @@ __device__ __forceinline__ void applyA64(const CGArgs& a, const double* __restri
     if (mask == kAllNeighbours) stencil_pairs<true>(c_stencil, load, mask, o0, o1, o2);
     else stencil_pairs<false>(c_stencil, load, mask, o0, o1, o2);
     o[0] = o0; o[1] = o1; o[2] = o2;
+}
+
+// ---- double-float residual (FP32-history mode)
+// A value is a pair hi + lo of floats (about 48 significant bits).  Error-free
+// transformations in FP32 with round-to-nearest intrinsics (never contracted into
+// FMAs): Knuth's two-sum gives s + e = a + b exactly, and fma(a, b, -a*b) is the exact
+// error of the product a*b.  Products keep the hi*lo cross terms and drop lo*lo; sums
+// are accumulated without renormalising the low part.  GB300 issues FP64 at about 1/64
+// of the FP32 rate, so a residual in these terms costs far fewer issue slots than in
+// FP64, at a relative accuracy (~1e-14) four orders below the FP32-history tolerance.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// (oh, ol) -= (sh + sl) (xh + xl)
+__device__ __forceinline__ void df_msub(float sh, float sl, float xh, float xl, float& oh,
+                                        float& ol) {
+    const float p = __fmul_rn(sh, xh);
+    const float pe = __fadd_rn(__fmaf_rn(sh, xh, -p), __fmaf_rn(sh, xl, __fmul_rn(sl, xh)));
+    float s, e;
+    df_two_sum(oh, -p, s, e);
+    oh = s;
+    ol = __fadd_rn(ol, __fsub_rn(e, pe));
+}
+// (sh, sl) += (vh, vl)
+__device__ __forceinline__ void df_add(float& sh, float& sl, float vh, float vl) {
+    float s, e;
+    df_two_sum(sh, vh, s, e);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(vl, e));
+}
+__device__ __forceinline__ void df_split(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// pair EP, 26 - EP in double-float (same zero pattern as stencil_pair)
+template <int EP, bool FULL, typename V>
+__device__ __forceinline__ void stencil_pair_df(V&& load, int mask, float* oh, float* ol) {
+    constexpr int EM = 26 - EP;
+    constexpr int ex = EP % 3 - 1, ey = (EP / 3) % 3 - 1, ez = EP / 9 - 1;
+    float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
+    if (FULL || (mask & (1 << EP))) load(std::integral_constant<int, EP>(), sh, sl);
+    if (FULL || (mask & (1 << EM))) load(std::integral_constant<int, EM>(), sh, sl);
+    const float* H = c_st32 + EP * 6;
+    const float* L = c_stl + EP * 6;
+    df_msub(H[0], L[0], sh[0], sl[0], oh[0], ol[0]);
+    df_msub(H[1], L[1], sh[1], sl[1], oh[1], ol[1]);
+    df_msub(H[2], L[2], sh[2], sl[2], oh[2], ol[2]);
+    if constexpr (ex != 0 && ey != 0) {
+        df_msub(H[3], L[3], sh[1], sl[1], oh[0], ol[0]);
+        df_msub(H[3], L[3], sh[0], sl[0], oh[1], ol[1]);
+    }
+    if constexpr (ex != 0 && ez != 0) {
+        df_msub(H[4], L[4], sh[2], sl[2], oh[0], ol[0]);
+        df_msub(H[4], L[4], sh[0], sl[0], oh[2], ol[2]);
+    }
+    if constexpr (ey != 0 && ez != 0) {
+        df_msub(H[5], L[5], sh[2], sl[2], oh[1], ol[1]);
+        df_msub(H[5], L[5], sh[1], sl[1], oh[2], ol[2]);
+    }
+}
+
+template <bool FULL, typename V>
+__device__ __forceinline__ void stencil_pairs_df(V&& load, int mask, float* oh, float* ol) {
+    stencil_pair_df<14, FULL>(load, mask, oh, ol);
+    stencil_pair_df<15, FULL>(load, mask, oh, ol);
+    stencil_pair_df<16, FULL>(load, mask, oh, ol);
+    stencil_pair_df<17, FULL>(load, mask, oh, ol);
+    stencil_pair_df<18, FULL>(load, mask, oh, ol);
+    stencil_pair_df<19, FULL>(load, mask, oh, ol);
+    stencil_pair_df<20, FULL>(load, mask, oh, ol);
+    stencil_pair_df<21, FULL>(load, mask, oh, ol);
+    stencil_pair_df<22, FULL>(load, mask, oh, ol);
+    stencil_pair_df<23, FULL>(load, mask, oh, ol);
+    stencil_pair_df<24, FULL>(load, mask, oh, ol);
+    stencil_pair_df<25, FULL>(load, mask, oh, ol);
+    stencil_pair_df<26, FULL>(load, mask, oh, ol);
+}
+
+// r = b - A x at an active voxel in double-float, rounded to FP32
+__device__ __forceinline__ float4 residual_df(const CGArgs& a, int m, int mask) {
+    float oh[3] = {0.f, 0.f, 0.f}, ol[3] = {0.f, 0.f, 0.f};   // o = A x
+    const float4 ch = a.xh[m], cl = a.xl[m];
+    const float dh = a.diag32[m], dl = a.diag_lo[m];
+    const float* H0 = c_st32 + 13 * 6;
+    const float* L0 = c_stl + 13 * 6;
+    // centre block: (d - G_0(0)) x; G_0(0) is diagonal (parity)
+    df_msub(-dh, -dl, ch.x, cl.x, oh[0], ol[0]);
+    df_msub(-dh, -dl, ch.y, cl.y, oh[1], ol[1]);
+    df_msub(-dh, -dl, ch.z, cl.z, oh[2], ol[2]);
+    df_msub(H0[0], L0[0], ch.x, cl.x, oh[0], ol[0]);
+    df_msub(H0[1], L0[1], ch.y, cl.y, oh[1], ol[1]);
+    df_msub(H0[2], L0[2], ch.z, cl.z, oh[2], ol[2]);
+    auto load = [&](auto e, float* sh, float* sl) {
+        const int m2 = m + c_noff[decltype(e)::value];
+        const float4 vh = a.xh[m2], vl = a.xl[m2];
+        df_add(sh[0], sl[0], vh.x, vl.x);
+        df_add(sh[1], sl[1], vh.y, vl.y);
+        df_add(sh[2], sl[2], vh.z, vl.z);
+    };
+    // o = (d - G_0(0)) x - sum_pairs G_0(e) (x_e + x_-e) = A x
+    if (mask == kAllNeighbours) stencil_pairs_df<true>(load, mask, oh, ol);
+    else stencil_pairs_df<false>(load, mask, oh, ol);
+    const float4 bh = a.bh[m], bl = a.bl[m];
+    float r[3];
+    const float bhv[3] = {bh.x, bh.y, bh.z}, blv[3] = {bl.x, bl.y, bl.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float s, e;
+        df_two_sum(bhv[c], -oh[c], s, e);
+        r[c] = __fadd_rn(s, __fadd_rn(__fsub_rn(blv[c], ol[c]), e));
+    }
+    return make_float4(r[0], r[1], r[2], 0.f);
 }
 
 // One Chebyshev pass on 8^3 tiles: d_k (with a one-voxel halo, zero outside the grid)
@@ -309,7 +432,10 @@ __device__ __forceinline__ double grid_total(const double* red, int nb) {
 // Mixed-precision iterative refinement: FP64 residual r = b - A x, FP32 conjugate
 // gradients for A e = r / ||r|| to a relative ~1e-5, x += ||r|| e; repeat until the
 // FP64 residual meets tol ||b||.  All blocks take identical decisions because every
-// block sums the same per-block partials in the same order.
+// block sums the same per-block partials in the same order.  DF: the residual is
+// evaluated in double-float arithmetic on float-pair copies of x and b (FP32-history
+// mode); x is split at entry, corrected in pairs and merged back to FP64 at exit.
+template <bool DF>
 __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
     cg::grid_group grid = cg::this_grid();
     const long long M = a.M;
@@ -320,21 +446,47 @@ __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
     double* red1 = a.red + nb;
     double bb = 0.0, rr = 0.0;
     int its = 0, outer = 0;
-    bool first = true, converged = false;
+    bool first = true, converged = false, zeroed = false;
+    if (DF) {
+        for (long long i = t0; i < a.nact; i += gs) {
+            const int m = a.act[i];
+            float4 h, l;
+            df_split(a.x[m], h.x, l.x);
+            df_split(a.x[M + m], h.y, l.y);
+            df_split(a.x[2 * M + m], h.z, l.z);
+            h.w = l.w = 0.f;
+            a.xh[m] = h;
+            a.xl[m] = l;
+            df_split(a.b[m], h.x, l.x);
+            df_split(a.b[M + m], h.y, l.y);
+            df_split(a.b[2 * M + m], h.z, l.z);
+            a.bh[m] = h;
+            a.bl[m] = l;
+        }
+        grid.sync();
+    }
     while (true) {
-        // ---- FP64 residual
+        // ---- residual (FP64, or double-float rounded to FP32)
         double rr_p = 0.0, bb_p = 0.0;
         for (long long i = t0; i < a.nact; i += gs) {
             const int m = a.act[i];
-            double o[3];
-            applyA64(a, a.x, m, a.nmask[i], o);
-            const double b0 = a.b[m], b1 = a.b[M + m], b2 = a.b[2 * M + m];
-            const double r0 = b0 - o[0], r1 = b1 - o[1], r2 = b2 - o[2];
-            rr_p += r0 * r0 + r1 * r1 + r2 * r2;
-            if (first) bb_p += b0 * b0 + b1 * b1 + b2 * b2;
-            a.r64[m] = r0;
-            a.r64[M + m] = r1;
-            a.r64[2 * M + m] = r2;
+            if (first) {
+                const double b0 = a.b[m], b1 = a.b[M + m], b2 = a.b[2 * M + m];
+                bb_p += b0 * b0 + b1 * b1 + b2 * b2;
+            }
+            if (DF) {
+                const float4 r = residual_df(a, m, a.nmask[i]);
+                rr_p += (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
+                a.r[m] = r;
+            } else {
+                double o[3];
+                applyA64(a, a.x, m, a.nmask[i], o);
+                const double r0 = a.b[m] - o[0], r1 = a.b[M + m] - o[1], r2 = a.b[2 * M + m] - o[2];
+                rr_p += r0 * r0 + r1 * r1 + r2 * r2;
+                a.r64[m] = r0;
+                a.r64[M + m] = r1;
+                a.r64[2 * M + m] = r2;
+            }
         }
         block_sum2(rr_p, bb_p);
         if (threadIdx.x == 0) { red0[blockIdx.x] = rr_p; red1[blockIdx.x] = bb_p; }
@@ -349,7 +501,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
                 a.x[m] = 0.0; a.x[M + m] = 0.0; a.x[2 * M + m] = 0.0;
             }
             rr = 0.0;
-            converged = true;
+            converged = zeroed = true;
             break;
         }
         if (rr <= a.tol2 * bb) { converged = true; break; }
@@ -363,10 +515,17 @@ __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
         const int n_it = min(a.n_cheb, max(3, (int)ceil(log(0.5 * need) / a.log_rate)));
         // normalise in FP64 first: a tiny residual must not underflow in FP32
         const double sc = 1.0 / sqrt(rr);
+        const float sc32 = (float)sc;
         for (long long i = t0; i < a.nact; i += gs) {
             const int m = a.act[i];
-            const float4 rv = make_float4((float)(a.r64[m] * sc), (float)(a.r64[M + m] * sc),
-                                          (float)(a.r64[2 * M + m] * sc), 0.f);
+            float4 rv;
+            if (DF) {
+                rv = a.r[m];
+                rv.x *= sc32; rv.y *= sc32; rv.z *= sc32;
+            } else {
+                rv = make_float4((float)(a.r64[m] * sc), (float)(a.r64[M + m] * sc),
+                                 (float)(a.r64[2 * M + m] * sc), 0.f);
+            }
             a.r[m] = rv;
             a.p[m] = make_float4(rv.x * a.inv_theta, rv.y * a.inv_theta, rv.z * a.inv_theta, 0.f);
             a.e[m] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -380,17 +539,43 @@ __global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
             float4* t = dk; dk = dn; dn = t;
         }
         its += n_it;
-        // ---- FP64 correction
+        // ---- correction x += ||r|| e (FP64, or in float pairs)
         const double back = sqrt(rr);
+        float bkh, bkl;
+        df_split(back, bkh, bkl);
         for (long long i = t0; i < a.nact; i += gs) {
             const int m = a.act[i];
             const float4 ev = a.e[m];
-            a.x[m] += back * (double)ev.x;
-            a.x[M + m] += back * (double)ev.y;
-            a.x[2 * M + m] += back * (double)ev.z;
+            if (DF) {
+                float4 h = a.xh[m], l = a.xl[m];
+                const float ec[3] = {ev.x, ev.y, ev.z};
+                float hc[3] = {h.x, h.y, h.z}, lc[3] = {l.x, l.y, l.z};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float p = __fmul_rn(bkh, ec[c]);
+                    const float pe = __fmaf_rn(bkh, ec[c], -p) + __fmul_rn(bkl, ec[c]);
+                    df_add(hc[c], lc[c], p, pe);
+                }
+                a.xh[m] = make_float4(hc[0], hc[1], hc[2], 0.f);
+                a.xl[m] = make_float4(lc[0], lc[1], lc[2], 0.f);
+            } else {
+                a.x[m] += back * (double)ev.x;
+                a.x[M + m] += back * (double)ev.y;
+                a.x[2 * M + m] += back * (double)ev.z;
+            }
         }
         grid.sync();
         ++outer;
+    }
+    if (DF && !zeroed) {   // x = hi + lo back in FP64
+        for (long long i = t0; i < a.nact; i += gs) {
+            const int m = a.act[i];
+            const float4 h = a.xh[m], l = a.xl[m];
+            a.x[m] = (double)h.x + (double)l.x;
+            a.x[M + m] = (double)h.y + (double)l.y;
+            a.x[2 * M + m] = (double)h.z + (double)l.z;
+        }
+        grid.sync();
     }
     // norm of the solution (all voxels, active and not)
     double xx = 0.0, dummy = 0.0;
@@ -606,8 +791,13 @@ void stencil_setup(mot_ctx* c) {
             }
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stencil, c->stencil, sizeof(double) * 27 * 6));
     float st32[27 * 6];
-    for (int k = 0; k < 27 * 6; ++k) st32[k] = (float)c->stencil[k];
+    float stl[27 * 6];
+    for (int k = 0; k < 27 * 6; ++k) {
+        st32[k] = (float)c->stencil[k];
+        stl[k] = (float)(c->stencil[k] - (double)st32[k]);
+    }
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_st32, st32, sizeof st32));
+    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stl, stl, sizeof stl));
     int noff[27];
     for (int ez = -1; ez <= 1; ++ez)
         for (int ey = -1; ey <= 1; ++ey)
@@ -619,7 +809,10 @@ void stencil_setup(mot_ctx* c) {
     for (int i = 0; i < c->n_taps; ++i) taps[i] = c->taps[i];
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_taps, taps, sizeof(double) * MAXTAPS));
     int per_sm = 0;
-    MOT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg, NT, 0));
+    if (c->precision == MOT_FP64)
+        MOT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<false>, NT, 0));
+    else
+        MOT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<true>, NT, 0));
     if (per_sm < 1) throw MotError{MOT_ERR_CUDA, "CG kernel cannot be made resident"};
     const long long need = (c->M + NT - 1) / NT;
     c->cg_blocks = (int)std::min<long long>((long long)per_sm * c->nsm, std::max<long long>(need, 1));
@@ -776,6 +969,16 @@ CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
     a.p = a.r + c->M;
     a.q = a.r + 2 * c->M;
     a.e = a.r + 3 * c->M;
+    a.xh = a.xl = a.bh = a.bl = nullptr;
+    a.diag_lo = nullptr;
+    if (c->cg_df) {
+        float4* d4 = reinterpret_cast<float4*>(c->cg_df);
+        a.xh = d4;
+        a.xl = d4 + c->M;
+        a.bh = d4 + 2 * c->M;
+        a.bl = d4 + 3 * c->M;
+        a.diag_lo = c->cg_df + 16 * c->M;
+    }
     a.red = c->red;
     a.tol2 = c->tol * c->tol;
     a.inv_theta = c->cheb_inv_theta;
@@ -793,13 +996,18 @@ CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
     return a;
 }
 
+void launch_cg(mot_ctx* c, void** args, cudaStream_t s) {
+    void* k = c->precision == MOT_FP64 ? (void*)k_cg<false> : (void*)k_cg<true>;
+    MOT_CUDA_TRY(cudaLaunchCooperativeKernel(k, c->cg_blocks, NT, args, 0, s));
+}
+
 // rhs + CG for step n; ||J_n||^2 into norm2_out (device), J_n in ring slot n
 void solve_step(mot_ctx* c, int n, const double* En, double* norm2_out, cudaStream_t s) {
     if (c->precision == MOT_FP64) epilogue<double>(c, n, En, s);
     else epilogue<float>(c, n, En, s);
     CGArgs a = make_cg_args(c, n, norm2_out);
     void* args[] = {&a};
-    MOT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_cg, c->cg_blocks, NT, args, 0, s));
+    launch_cg(c, args, s);
 }
 
 void read_aos(mot_ctx* c, const double* in_dev, double* slot, cudaStream_t s) {
@@ -835,7 +1043,7 @@ void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double*
     MOT_LAUNCH_CHECK();
     CGArgs a = make_cg_args(c, tau, norm2_out);
     void* args[] = {&a};
-    MOT_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_cg, c->cg_blocks, NT, args, 0, s));
+    launch_cg(c, args, s);
     double* mu = c->J + (long long)s0 * 3 * c->M;
     k_adj_vacuum<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->U, c->V, c->W, c->vfac, mu,
                                                            c->rhs, c->cg_q);
