@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--precision", default="both", choices=["both", "fp32_history", "fp64"])
     ap.add_argument("--config", default=CONFIG_NAME)
     ap.add_argument("--scheme", default="blocked", choices=["blocked", "direct"])
-    ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--block", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -132,24 +132,21 @@ def geometry(ctx):
     return Hu * Hv * Hw, Pw * Pv * Hu
 
 
-def mac_bytes_per_launch(ctx, precision, lags, with_acc):
+def mac_bytes_per_launch(ctx, precision, lags, n_levels):
     """Algorithmic bytes of one lag-MAC launch over `lags` lags: every lag reads the real
     kernel spectrum once per octant bin (6 values) and the three complex spectra of J
     at every rfft bin; the result (3 complex) is written once per rfft bin; with the
-    blocked scheme the step's far-lag accumulator is read and cleared (2 x 3 complex)."""
+    blocked scheme each far level's accumulator entry of the step is read (3 complex)."""
     s = 8 if precision == "fp64" else 4
     noct, nbins = geometry(ctx)
-    b = lags * (6 * s * noct + 6 * s * nbins) + 6 * s * nbins
-    if with_acc:
-        b += 2 * 6 * s * nbins
-    return b
+    return lags * (6 * s * noct + 6 * s * nbins) + 6 * s * nbins * (1 + n_levels)
 
 
 def far_bytes_per_period(ctx, precision):
     """Algorithmic bytes of every block Toeplitz launch of one period (each level S
     fires S_max / S times): the window of min(2S - 1, ell) past spectra (3 complex per
     bin), the level's temporal kernel spectra (S + 1 frequencies x 6 complex per
-    octant bin), and a read-modify-write of S future accumulators (3 complex per bin)."""
+    octant bin), and the S future accumulators it writes (3 complex per bin)."""
     c = 16 if precision == "fp64" else 8
     noct, nbins = geometry(ctx)
     levels = ctx.levels
@@ -159,7 +156,7 @@ def far_bytes_per_period(ctx, precision):
     total, launches = 0, 0
     for S in levels:
         lmax = min(2 * S - 1, ctx.ell)
-        per = 3 * c * nbins * lmax + (S + 1) * 6 * c * noct + 2 * S * 3 * c * nbins
+        per = 3 * c * nbins * lmax + (S + 1) * 6 * c * noct + S * 3 * c * nbins
         total += per * (smax // S)
         launches += smax // S
     return total, launches
@@ -237,7 +234,8 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
     peak, peak_kind = measured_peaks()
     # dominant kernel of the history evaluation
     mac_lags = min(block - 1, ctx.ell) if scheme == "blocked" else ctx.ell
-    mac_b = mac_bytes_per_launch(ctx, prec, mac_lags, scheme == "blocked")
+    mac_b = mac_bytes_per_launch(ctx, prec, mac_lags,
+                                 len(ctx.levels) if scheme == "blocked" else 0)
     mac_ms = st["ms_mac"] / max(st["mac_launches"], 1)
     cands = [("k_mac", mac_b, mac_ms, st["ms_mac"])]
     if scheme == "blocked" and st["far_launches"]:
@@ -381,8 +379,8 @@ def main():
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 history (FFT, spectra, lag products) + f64 (elements, FIR, CG residual)"
-                 if prec == "fp32_history" else "f64",
+        "dtype": "f32 history (FFT, spectra, lag products, inner CG) + double-float CG "
+                 "residual + f64 (elements, FIR, state J)" if prec == "fp32_history" else "f64",
         "data": "synthetic",
         "config": {"workload": "sphere eps_r=12, %d^3 voxels (%d), c dt = h, hp9 FIR "
                                "delta=1e-7*M, +z x-polarised modulated Gaussian plane wave"

@@ -718,6 +718,185 @@ void far_launch_reg(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     MOT_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- four-step variant
+// Levels with 2S = P > 32 (FP32) / 16 (FP64): the temporal transform of length
+// P = T Q1 is split as n = t + T n2, k = k2 + Q1 k1 (Bailey's four-step form):
+//   X[k2 + Q1 k1] = sum_t W_T^{t k1} W_P^{t k2} sum_{n2} x[t + T n2] W_Q1^{n2 k2}.
+// Phase A: a thread per (component, bin, t) loads its time-strided subsequence and
+//   runs the Q1-point transform in registers (literal twiddles); the results go to
+//   shared memory, XOR-swizzled by lane so that the warp's 32 rows hit 32 banks.
+// Phase B: an item per (bin, k2) gathers the three components over t, applies
+//   W_P^{t k2} (powers of one table root), the T-point transforms, the 3x3 product
+//   with the level spectra, the inverse T-point transforms and the conjugate
+//   twiddles, and writes back in place.
+// Phase C: the thread of phase A runs the inverse Q1-point transform and stores its
+//   outputs in the second half of the window (times n0 .. n0 + S - 1).
+// A block is 256 threads: phases A and C use 3 NB T = 192 of them, phase B all.
+template <typename R, int P> struct Far4 {
+    typedef typename CT<R>::c C;
+    static constexpr int Q1 = sizeof(R) == 4 ? 32 : 16;
+    static constexpr int T = P / Q1;
+    static constexpr int NB = (sizeof(R) == 4 ? 2048 : 1024) / P;
+    static constexpr int S = P / 2;
+    static constexpr int NA = 3 * NB * T;
+    static constexpr int NI = NB * Q1;
+    static constexpr int NTB = 256;
+    static_assert(NA == 192 && T >= 2 && Q1 * T == P, "four-step shape");
+    struct Smem {
+        C Y[3 * NB * T][Q1];      // row (c NB + bin) T + t, column k2 ^ key(row)
+        C H[S + 1][7 * NB];       // level spectra [w][c NB + bin], rows padded by NB
+        C tw[Q1];                 // W_P^{k2}
+        int in[P];                // ring slot of every window time (-1: none)
+        int out[S];               // accumulator slot of every output time
+    };
+    // phase-A thread of (component, t, bin); its lane (index mod 32) keys the swizzle
+    __device__ static int athread(int c, int t, int bin) { return (c * T + t) * NB + bin; }
+    __device__ static int row(int c, int t, int bin) { return (c * NB + bin) * T + t; }
+    __device__ static int col(int k2, int a) { return k2 ^ (a & (Q1 - 1)); }
+};
+
+template <typename R, int P>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_far_4s(FarArgs<R> a) {
+    typedef Far4<R, P> F;
+    typedef typename F::C C;
+    constexpr int Q1 = F::Q1, T = F::T, NB = F::NB, S = F::S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename F::Smem& sm = *reinterpret_cast<typename F::Smem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int ut = blockIdx.x % a.ntile;
+    const int rest = blockIdx.x / a.ntile;
+    const int mirror = rest & 3;
+    const int orow = rest >> 2;
+    const int kv_o = orow % a.Hv, kw_o = orow / a.Hv;
+    const bool fv = (mirror & 1) != 0, fw = (mirror & 2) != 0;
+    const bool mv = kv_o > 0 && 2 * kv_o < a.Pv;
+    const bool mw = kw_o > 0 && 2 * kw_o < a.Pw;
+    if ((fv && !mv) || (fw && !mw)) return;
+    const int kv = fv ? a.Pv - kv_o : kv_o;
+    const int kw = fw ? a.Pw - kw_o : kw_o;
+    const int ku0 = ut * NB;
+    const int nlive = min(NB, a.Hu - ku0);
+    const long long row0 = ((long long)kw * a.Pv + kv) * a.Hu + ku0;
+    const long long obase = ((long long)kw_o * a.Hv + kv_o) * a.Hu + ku0;
+    for (int i = tid; i < (S + 1) * 6 * NB; i += F::NTB) {
+        const int l = i % NB, wc = i / NB;      // wc = w * 6 + c
+        if (l < nlive)
+            cp_async_c(&sm.H[wc / 6][(wc % 6) * NB + l], a.H + (long long)wc * a.noct + obase + l);
+    }
+    const int tfirst = max(1, a.n0 - a.lmax);
+    for (int i = tid; i < P; i += F::NTB) {
+        const int time = a.n0 - P + i;
+        sm.in[i] = time >= tfirst ? time % a.hring : -1;
+        if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
+        if (i < Q1) sm.tw[i] = a.tw[i];     // W_P^i
+    }
+    __syncthreads();
+    // ---- phase A
+    const int bin = tid % NB, ct = tid / NB;
+    const int t = ct % T, comp = ct / T;
+    const bool athr = tid < F::NA;
+    const bool live = athr && bin < nlive;
+    const R sig = comp == 0 ? (R)1 : (comp == 1 ? (fv ? (R)-1 : (R)1) : (fw ? (R)-1 : (R)1));
+    C x[Q1];
+    if (athr) {
+        Unroll<0, Q1>::run([&](auto q) {
+            constexpr int n2 = decltype(q)::value;
+            const int slot = sm.in[t + T * n2];
+            C v;
+            v.x = 0; v.y = 0;
+            if (slot >= 0 && live) v = a.ring[((long long)slot * 3 + comp) * a.nbins + row0 + bin];
+            v.x *= sig; v.y *= sig;
+            x[n2] = v;
+        });
+        fft_dif_reg<C, Q1, 1, -1>(x, sm.tw, 0);      // register j holds k2 = bitrev(j)
+        C* yr = sm.Y[F::row(comp, t, bin)];
+        Unroll<0, Q1>::run([&](auto q) {
+            constexpr int j = decltype(q)::value;
+            yr[F::col(bitrev<Q1>(j), tid)] = x[j];
+        });
+    }
+    cp_async_commit_wait();
+    __syncthreads();
+    // ---- phase B
+    for (int it = tid; it < F::NI; it += F::NTB) {
+        const int b = it % NB, k2 = it / NB;
+        C wt[T];                                 // W_P^{t k2}
+        wt[0].x = 1; wt[0].y = 0;
+        wt[1] = sm.tw[k2];
+        Unroll<2, T>::run([&](auto q) {
+            constexpr int tt = decltype(q)::value;
+            wt[tt] = cmul(wt[tt - 1], wt[1]);
+        });
+        C v[3][T];
+        Unroll<0, 3>::run([&](auto cq) {
+            constexpr int c = decltype(cq)::value;
+            Unroll<0, T>::run([&](auto q) {
+                constexpr int tt = decltype(q)::value;
+                v[c][tt] = cmul(sm.Y[F::row(c, tt, b)][F::col(k2, F::athread(c, tt, b))], wt[tt]);
+            });
+            fft_dif_reg<C, T, 1, -1>(v[c], sm.tw, 0);   // register j holds k1 = bitrev(j)
+        });
+        Unroll<0, T>::run([&](auto q) {
+            constexpr int j = decltype(q)::value;
+            const int w = k2 + Q1 * bitrev<T>(j);
+            const bool cj = w > S;
+            const int ws = cj ? P - w : w;
+            const C* hp = &sm.H[ws][b];
+            C h[6];
+#pragma unroll
+            for (int cc = 0; cc < 6; ++cc) {
+                h[cc] = hp[cc * NB];
+                if (cj) h[cc].y = -h[cc].y;
+            }
+            const C x0 = v[0][j], x1 = v[1][j], x2 = v[2][j];
+            v[0][j] = cadd(cadd(cmul(h[0], x0), cmul(h[3], x1)), cmul(h[4], x2));
+            v[1][j] = cadd(cadd(cmul(h[3], x0), cmul(h[1], x1)), cmul(h[5], x2));
+            v[2][j] = cadd(cadd(cmul(h[4], x0), cmul(h[5], x1)), cmul(h[2], x2));
+        });
+        Unroll<0, 3>::run([&](auto cq) {
+            constexpr int c = decltype(cq)::value;
+            fft_dit_reg<C, T, 1, +1>(v[c], sm.tw, 0);   // register t holds C_t
+            Unroll<0, T>::run([&](auto q) {
+                constexpr int tt = decltype(q)::value;
+                C w = wt[tt];
+                w.y = -w.y;
+                sm.Y[F::row(c, tt, b)][F::col(k2, F::athread(c, tt, b))] = cmul(v[c][tt], w);
+            });
+        });
+    }
+    __syncthreads();
+    // ---- phase C
+    if (!live) return;
+    const C* yr = sm.Y[F::row(comp, t, bin)];
+    Unroll<0, Q1>::run([&](auto q) {
+        constexpr int j = decltype(q)::value;
+        x[j] = yr[F::col(bitrev<Q1>(j), tid)];
+    });
+    fft_dit_reg<C, Q1, 1, +1>(x, sm.tw, 0);          // register n2 holds y[t + T n2]
+    const R scale = sig / (R)P;
+    Unroll<Q1 / 2, Q1>::run([&](auto q) {
+        constexpr int n2 = decltype(q)::value;
+        const int pos = t + T * n2;                  // >= S
+        C v = x[n2];
+        v.x *= scale; v.y *= scale;
+        a.acc[((long long)sm.out[pos - S] * 3 + comp) * a.nbins + row0 + bin] = v;
+    });
+}
+
+template <typename R, int P>
+void far_launch_4s(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
+    typedef Far4<R, P> F;
+    const int sm_bytes = (int)sizeof(typename F::Smem);
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far_4s<R, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      sm_bytes));
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far_4s<R, P>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    a.ntile = (c->Hu + F::NB - 1) / F::NB;
+    const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
+    k_far_4s<R, P><<<(int)blocks, F::NTB, sm_bytes, s>>>(a);
+    MOT_LAUNCH_CHECK();
+}
+
 template <typename R, int TB>
 void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     typedef typename CT<R>::c C;
@@ -755,18 +934,18 @@ void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
     a.tw = twtab<R>(f);
     // lines per CTA: 3 components x TB bins; fewer bins for long levels keeps several
     // CTAs resident per SM
-    // register-resident lines: up to 32 (FP32) / 16 (FP64) points per thread, a line of
-    // 2S points split over 2S / Q threads (at most 8, 16 (FP64) for S = 128); the
-    // shared-memory kernel beyond
+    // lines of up to 32 (FP32) / 16 (FP64) points: one thread per line, in registers;
+    // longer lines: the four-step kernel (FP64 S = 128: lines split over 8 lanes with
+    // shuffle stages); beyond S = 128 the shared-memory Stockham kernel
     if constexpr (std::is_same<R, float>::value) {
         switch (a.S) {
             case 2: far_launch_reg<R, 4, 1>(c, a, s); break;
             case 4: far_launch_reg<R, 8, 1>(c, a, s); break;
             case 8: far_launch_reg<R, 16, 1>(c, a, s); break;
             case 16: far_launch_reg<R, 32, 1>(c, a, s); break;
-            case 32: far_launch_reg<R, 32, 2>(c, a, s); break;
-            case 64: far_launch_reg<R, 32, 4>(c, a, s); break;
-            case 128: far_launch_reg<R, 32, 8>(c, a, s); break;
+            case 32: far_launch_4s<R, 64>(c, a, s); break;
+            case 64: far_launch_4s<R, 128>(c, a, s); break;
+            case 128: far_launch_4s<R, 256>(c, a, s); break;
             default: far_launch<R, 4>(c, a, s);
         }
     } else {
@@ -774,9 +953,9 @@ void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
             case 2: far_launch_reg<R, 4, 1>(c, a, s); break;
             case 4: far_launch_reg<R, 8, 1>(c, a, s); break;
             case 8: far_launch_reg<R, 16, 1>(c, a, s); break;
-            case 16: far_launch_reg<R, 16, 2>(c, a, s); break;
-            case 32: far_launch_reg<R, 16, 4>(c, a, s); break;
-            case 64: far_launch_reg<R, 16, 8>(c, a, s); break;
+            case 16: far_launch_4s<R, 32>(c, a, s); break;
+            case 32: far_launch_4s<R, 64>(c, a, s); break;
+            case 64: far_launch_4s<R, 128>(c, a, s); break;
             case 128: far_launch_reg<R, 32, 8>(c, a, s); break;
             default: far_launch<R, 2>(c, a, s);
         }
