@@ -24,6 +24,7 @@ using namespace mot_fft;
 namespace {
 
 constexpr int NT = 256;
+constexpr int kLoadBatch = 8;   // global loads a thread keeps in flight while staging a tile
 
 // lines per CTA: 8 (FP64) / 16 (FP32) keeps the shared tile near 60 KB at P = 210,
 // so that several CTAs are resident per SM
@@ -49,26 +50,39 @@ __global__ void __launch_bounds__(NT) k_fwd_x(const double* __restrict__ in, int
     const long long npairs = 3LL * W * VP;
     const long long pair0 = (long long)blockIdx.x * TB;
     load_tw(stw, tw, P);
-    // load: z = a + i b, zero-padded
-    for (int it = threadIdx.x; it < TB * P; it += blockDim.x) {
-        const int t = it / P, j = it % P;
-        const long long pr = pair0 + t;
-        C z;
-        z.x = 0; z.y = 0;
-        if (pr < npairs && j < U) {
-            const long long cw = pr / VP;
-            const int v = (int)(pr % VP) * 2;
-            const double* row = in + (cw * V + v) * (long long)U;
-            if (scale) {   // per-voxel factor (the adjoint transforms chi * lambda)
-                const long long m0 = ((cw % W) * V + v) * (long long)U + j;
-                z.x = (R)(row[j] * scale[m0]);
-                if (v + 1 < V) z.y = (R)(row[U + j] * scale[m0 + U]);
-            } else {
-                z.x = (R)row[j];
-                if (v + 1 < V) z.y = (R)row[U + j];
+    // load: z = a + i b, zero-padded; batches of kLoadBatch loads in flight per thread
+    for (int it0 = threadIdx.x; it0 < TB * P; it0 += kLoadBatch * blockDim.x) {
+        double va[kLoadBatch], vb[kLoadBatch];
+#pragma unroll
+        for (int q = 0; q < kLoadBatch; ++q) {
+            const int it = it0 + q * blockDim.x;
+            const int t = it / P, j = it % P;
+            const long long pr = pair0 + t;
+            va[q] = 0.0;
+            vb[q] = 0.0;
+            if (it < TB * P && pr < npairs && j < U) {
+                const long long cw = pr / VP;
+                const int v = (int)(pr % VP) * 2;
+                const double* row = in + (cw * V + v) * (long long)U;
+                va[q] = row[j];
+                if (v + 1 < V) vb[q] = row[U + j];
+                if (scale) {   // per-voxel factor (the adjoint transforms chi * lambda)
+                    const long long m0 = ((cw % W) * V + v) * (long long)U + j;
+                    va[q] *= scale[m0];
+                    if (v + 1 < V) vb[q] *= scale[m0 + U];
+                }
             }
         }
-        b0[j * ld + t] = z;
+#pragma unroll
+        for (int q = 0; q < kLoadBatch; ++q) {
+            const int it = it0 + q * blockDim.x;
+            if (it >= TB * P) break;
+            const int t = it / P, j = it % P;
+            C z;
+            z.x = (R)va[q];
+            z.y = (R)vb[q];
+            b0[j * ld + t] = z;
+        }
     }
     __syncthreads();
     C* res = fft_tile<C, TB>(b0, b1, P, rl.r, rl.n, ld, stw, -1);
@@ -110,26 +124,37 @@ __global__ void __launch_bounds__(NT) k_inv_x(const typename CT<R>::c* __restric
     const long long npairs = 3LL * W * VP;
     const long long pair0 = (long long)blockIdx.x * TB;
     load_tw(stw, tw, P);
-    for (int it = threadIdx.x; it < TB * Hu; it += blockDim.x) {
-        const int t = it / Hu, k = it % Hu;
-        const long long pr = pair0 + t;
-        C A, B;
-        A.x = 0; A.y = 0; B.x = 0; B.y = 0;
-        if (pr < npairs) {
-            const long long cw = pr / VP;
-            const int v = (int)(pr % VP) * 2;
-            A = in[(cw * V + v) * (long long)Hu + k];
-            if (v + 1 < V) B = in[(cw * V + v + 1) * (long long)Hu + k];
+    for (int it0 = threadIdx.x; it0 < TB * Hu; it0 += kLoadBatch * blockDim.x) {
+        C Aq[kLoadBatch], Bq[kLoadBatch];
+#pragma unroll
+        for (int q = 0; q < kLoadBatch; ++q) {
+            const int it = it0 + q * blockDim.x;
+            const int t = it / Hu, k = it % Hu;
+            const long long pr = pair0 + t;
+            Aq[q].x = 0; Aq[q].y = 0; Bq[q].x = 0; Bq[q].y = 0;
+            if (it < TB * Hu && pr < npairs) {
+                const long long cw = pr / VP;
+                const int v = (int)(pr % VP) * 2;
+                Aq[q] = in[(cw * V + v) * (long long)Hu + k];
+                if (v + 1 < V) Bq[q] = in[(cw * V + v + 1) * (long long)Hu + k];
+            }
         }
-        C z;
-        z.x = A.x - B.y;
-        z.y = A.y + B.x;
-        b0[k * ld + t] = z;
-        if (k >= 1 && k < P - k) {
-            C zm;
-            zm.x = A.x + B.y;
-            zm.y = B.x - A.y;
-            b0[(P - k) * ld + t] = zm;
+#pragma unroll
+        for (int q = 0; q < kLoadBatch; ++q) {
+            const int it = it0 + q * blockDim.x;
+            if (it >= TB * Hu) break;
+            const int t = it / Hu, k = it % Hu;
+            const C A = Aq[q], B = Bq[q];
+            C z;
+            z.x = A.x - B.y;
+            z.y = A.y + B.x;
+            b0[k * ld + t] = z;
+            if (k >= 1 && k < P - k) {
+                C zm;
+                zm.x = A.x + B.y;
+                zm.y = B.x - A.y;
+                b0[(P - k) * ld + t] = zm;
+            }
         }
     }
     __syncthreads();
@@ -178,11 +203,10 @@ __global__ void __launch_bounds__(NT) k_mid(const typename CT<R>::c* __restrict_
     load_tw(stw, tw, P);
     for (int it = threadIdx.x; it < P * TB; it += blockDim.x) {
         const int j = it / TB, t = it % TB;
-        C z;
-        z.x = 0; z.y = 0;
-        if (j < a.n_in && ku0 + t < a.Hu) z = src[j * a.in_a + t];
-        b0[j * ld + t] = z;
+        const bool ok = j < a.n_in && ku0 + t < a.Hu;
+        cp_async_c(&b0[j * ld + t], ok ? src + j * a.in_a + t : src, ok);
     }
+    cp_async_commit_wait();
     __syncthreads();
     C* res = fft_tile<C, TB>(b0, b1, P, rl.r, rl.n, ld, stw, a.dir);
     for (int it = threadIdx.x; it < a.n_out * TB; it += blockDim.x) {
@@ -208,8 +232,11 @@ template <typename R> size_t smem_bytes(int P) {
     return sizeof(C) * ((size_t)P + 2 * (size_t)P * (Tile<R>::TB + 1));
 }
 
+// dynamic shared memory of a pass kernel; prefer the largest shared-memory carveout so
+// that several of its tiles are resident per SM
 template <typename K> void set_smem(K kern, size_t bytes) {
     MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
 }
 
 __global__ void twiddle_kernel(int P, double2* t64, float2* t32) {

@@ -6,7 +6,62 @@
 
 #include "mot_internal.cuh"
 
+#include <type_traits>
+
 namespace mot_fft {
+
+// compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
+template <int B, int E> struct Unroll1 {
+    template <typename F> __device__ __forceinline__ static void run(F&& f) {
+        f(std::integral_constant<int, B>());
+        Unroll1<B + 1, E>::run(f);
+    }
+};
+template <int E> struct Unroll1<E, E> {
+    template <typename F> __device__ __forceinline__ static void run(F&&) {}
+};
+
+// Twiddles known at compile time: cos and sin of 2 pi k / n by the Taylor series of
+// sin and cos on [0, pi/4], after reducing the angle with the quadrant and octant
+// symmetries in exact integer arithmetic.  Evaluated only by the compiler (constexpr
+// initialisers), so butterflies with compile-time indices multiply by literal constants.
+struct CTw { double re, im; };
+__host__ __device__ constexpr double taylor_sin(double x) {
+    double term = x, sum = x;
+    for (int i = 1; i < 14; ++i) {
+        term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
+        sum += term;
+    }
+    return sum;
+}
+__host__ __device__ constexpr double taylor_cos(double x) {
+    double term = 1.0, sum = 1.0;
+    for (int i = 1; i < 14; ++i) {
+        term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
+        sum += term;
+    }
+    return sum;
+}
+// exp(-2 pi i k / n), 0 <= k < n
+__host__ __device__ constexpr CTw root_of_unity(int k, int n) {
+    constexpr double pi = 3.141592653589793238462643383279502884;
+    const int q = (4 * k) / n;               // quadrant of 2 pi k / n
+    const int r = 4 * k - q * n;             // remainder angle = (pi / 2) r / n, r in [0, n)
+    const bool hi = 2 * r > n;               // beyond pi / 4: use the complement
+    const double phi = (pi / 2.0) * (double)(hi ? n - r : r) / (double)n;
+    const double c0 = hi ? taylor_sin(phi) : taylor_cos(phi);
+    const double s0 = hi ? taylor_cos(phi) : taylor_sin(phi);
+    // angle = q pi/2 + (pi/2) r / n ; (cos, sin) of it
+    const double ca = q == 0 ? c0 : (q == 1 ? -s0 : (q == 2 ? -c0 : s0));
+    const double sa = q == 0 ? s0 : (q == 1 ? c0 : (q == 2 ? -s0 : -c0));
+    return CTw{ca, -sa};
+}
+static_assert(root_of_unity(0, 8).re == 1.0 && root_of_unity(2, 8).im == -1.0, "twiddle");
+static_assert(root_of_unity(4, 8).re == -1.0 && root_of_unity(6, 8).im == 1.0, "twiddle");
+static_assert(root_of_unity(1, 6).re - 0.5 < 1e-16 && 0.5 - root_of_unity(1, 6).re < 1e-16,
+              "twiddle");
+static_assert(root_of_unity(1, 8).re - 0.70710678118654752 < 2e-16 &&
+              0.70710678118654752 - root_of_unity(1, 8).re < 2e-16, "twiddle");
 
 // dir = -1 forward (exp(-i...)), +1 inverse; W(m) = exp(dir 2 pi i m / P) from table
 template <typename C>
@@ -33,10 +88,12 @@ __device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
         v[1] = cadd(a1, jb1);
         v[3] = csub(a1, jb1);
     } else {
-        // odd radix: out[q] = v0 + sum_r (s_r cos(2 pi q r/R) -/+ i d_r sin(2 pi q r/R))
+        // odd radix: out[q] = v0 + sum_r (s_r cos(2 pi q r/R) -/+ i d_r sin(2 pi q r/R)),
+        // with the cosines and sines as compile-time constants
+        typedef decltype(v[0].x) Rl;
         constexpr int H = (R - 1) / 2;
         C s[H], d[H];
-        C v0 = v[0];
+        const C v0 = v[0];
         C sum = v0;
 #pragma unroll
         for (int r = 1; r <= H; ++r) {
@@ -44,20 +101,19 @@ __device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
             d[r - 1] = csub(v[r], v[R - r]);
             sum = cadd(sum, s[r - 1]);
         }
-        const int step = P / R;
-#pragma unroll
-        for (int q = 1; q <= H; ++q) {
+        Unroll1<1, H + 1>::run([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
             C A = v0, B;
             B.x = 0; B.y = 0;
-#pragma unroll
-            for (int r = 1; r <= H; ++r) {
-                const C w = tw[((q * r) % R) * step];   // cos - i sin (forward table)
-                const auto cs = w.x, sn = -w.y;
+            Unroll1<1, H + 1>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr CTw w = root_of_unity((q * r) % R, R);   // cos - i sin
+                constexpr Rl cs = (Rl)w.re, sn = (Rl)(-w.im);
                 A.x += s[r - 1].x * cs;
                 A.y += s[r - 1].y * cs;
                 B.x += d[r - 1].x * sn;
                 B.y += d[r - 1].y * sn;
-            }
+            });
             // forward: out[q] = A - i B, out[R-q] = A + i B ; inverse: swapped
             C mB;   // -i B
             mB.x = B.y; mB.y = -B.x;
@@ -68,7 +124,7 @@ __device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
                 v[q] = csub(A, mB);
                 v[R - q] = cadd(A, mB);
             }
-        }
+        });
         v[0] = sum;
     }
 }
@@ -134,6 +190,23 @@ struct RadixList {
 template <typename C>
 __device__ __forceinline__ void load_tw(C* stw, const C* tw, int P) {
     for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+}
+
+// Asynchronous global -> shared copy of one complex value (8 or 16 bytes); with
+// valid = false nothing is read and the destination is zero-filled.  A tile's copies
+// are all issued before one wait, so their memory latencies overlap.
+template <typename C>
+__device__ __forceinline__ void cp_async_c(C* dst, const C* src, bool valid = true) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src),
+                     "r"(valid ? 8 : 0));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                     "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 

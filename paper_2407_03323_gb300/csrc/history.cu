@@ -234,12 +234,11 @@ __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
         const int i = it / L3, t = it % L3;
         const int comp = t / TB, bb = t % TB;
         const int slot = s_in[i];
-        C v;
-        v.x = 0; v.y = 0;
-        if (slot >= 0 && ku0 + bb < a.Hu)
-            v = a.ring[((long long)slot * 3 + comp) * a.nbins + row + bb];
-        b0[i * ld + t] = v;
+        const bool ok = slot >= 0 && ku0 + bb < a.Hu;
+        cp_async_c(&b0[i * ld + t],
+                   ok ? a.ring + ((long long)slot * 3 + comp) * a.nbins + row + bb : a.ring, ok);
     }
+    cp_async_commit_wait();
     __syncthreads();
     C* X = fft_tile<C, L3>(b0, b1, P, a.rl.r, a.rl.n, ld, stw, -1);
     C* other = (X == b0) ? b1 : b0;
@@ -397,48 +396,6 @@ template <int E> struct Unroll<E, E> {
     template <typename F> __device__ __forceinline__ static void run(F&&) {}
 };
 
-// Twiddles known at compile time: cos and sin of 2 pi k / n by the Taylor series of
-// sin and cos on [0, pi/4], after reducing the angle with the quadrant and octant
-// symmetries in exact integer arithmetic.  Evaluated only by the compiler (constexpr
-// initialisers), so the radix-2 stages below multiply by literal constants.
-struct CTw { double re, im; };
-__host__ __device__ constexpr double taylor_sin(double x) {
-    double term = x, sum = x;
-    for (int i = 1; i < 14; ++i) {
-        term *= -x * x / ((2.0 * i) * (2.0 * i + 1.0));
-        sum += term;
-    }
-    return sum;
-}
-__host__ __device__ constexpr double taylor_cos(double x) {
-    double term = 1.0, sum = 1.0;
-    for (int i = 1; i < 14; ++i) {
-        term *= -x * x / ((2.0 * i - 1.0) * (2.0 * i));
-        sum += term;
-    }
-    return sum;
-}
-// exp(-2 pi i k / n), 0 <= k < n
-__host__ __device__ constexpr CTw root_of_unity(int k, int n) {
-    constexpr double pi = 3.141592653589793238462643383279502884;
-    const int q = (4 * k) / n;               // quadrant of 2 pi k / n
-    const int r = 4 * k - q * n;             // remainder angle = (pi / 2) r / n, r in [0, n)
-    const bool hi = 2 * r > n;               // beyond pi / 4: use the complement
-    const double phi = (pi / 2.0) * (double)(hi ? n - r : r) / (double)n;
-    const double c0 = hi ? taylor_sin(phi) : taylor_cos(phi);
-    const double s0 = hi ? taylor_cos(phi) : taylor_sin(phi);
-    // angle = q pi/2 + (pi/2) r / n ; (cos, sin) of it
-    const double ca = q == 0 ? c0 : (q == 1 ? -s0 : (q == 2 ? -c0 : s0));
-    const double sa = q == 0 ? s0 : (q == 1 ? c0 : (q == 2 ? -s0 : -c0));
-    return CTw{ca, -sa};
-}
-static_assert(root_of_unity(0, 8).re == 1.0 && root_of_unity(2, 8).im == -1.0, "twiddle");
-static_assert(root_of_unity(4, 8).re == -1.0 && root_of_unity(6, 8).im == 1.0, "twiddle");
-static_assert(root_of_unity(1, 6).re - 0.5 < 1e-16 && 0.5 - root_of_unity(1, 6).re < 1e-16,
-              "twiddle");
-static_assert(root_of_unity(1, 8).re - 0.70710678118654752 < 2e-16 &&
-              0.70710678118654752 - root_of_unity(1, 8).re < 2e-16, "twiddle");
-
 // v * W_N^K for compile-time K, N; DIR = -1 forward (W = exp(-2 pi i / N)), +1 inverse
 template <int K, int N, int DIR, typename C>
 __device__ __forceinline__ C twiddle_c(C v) {
@@ -586,19 +543,6 @@ template <typename C, int Q, int T, int DIR>
 __device__ __forceinline__ void fft_dit_reg(C* x, const C* __restrict__ tw, int t) {
     DitLoc<C, Q, T, 2, DIR>::run(x);
     DitCross<C, Q, T, 1, DIR>::run(x, tw, t);
-}
-
-// asynchronous global -> shared copy of one complex value (8 or 16 bytes)
-template <typename C>
-__device__ __forceinline__ void cp_async_c(C* dst, const C* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (sizeof(C) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
-}
-__device__ __forceinline__ void cp_async_commit_wait() {
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <typename R, int Q, int T> struct FarRegSmem {
@@ -906,6 +850,7 @@ void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     if (sm > 220 * 1024 || a.S > kMaxLevel)
         throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
     MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
     k_far<R, TB><<<(int)blocks, NT, sm, s>>>(a);
     MOT_LAUNCH_CHECK();
