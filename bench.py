@@ -162,13 +162,13 @@ def far_bytes_per_period(ctx, precision):
     return total, launches
 
 
-def profile_traffic(config, precision, kernel):
+def profile_traffic(config, precision, scheme, kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if recorded
-    for this workload."""
+    for this workload, precision and history scheme."""
     p = os.path.join(ROOT, "profiles", "%s_%s.txt" % (kernel, config))
     if not os.path.exists(p):
         return None
-    key = "traffic_bytes_per_launch_%s:" % precision
+    key = "traffic_bytes_per_launch_%s_%s:" % (precision, scheme)
     for line in open(p):
         if line.startswith(key):
             try:
@@ -260,7 +260,7 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
         "roofline": {"bound": "hbm" if prec == "fp32_history" else "fp64-alu (hbm shown)",
                      "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": profile_traffic(args.config, prec, name),
+                     "traffic": profile_traffic(args.config, prec, scheme, name),
                      "algorithmic_bytes_per_launch": b_launch},
         "clocks": clocks, "ell": info["ell"], "P": list(info["P"]), "levels": ctx.levels,
     }

@@ -156,4 +156,12 @@ def config(name):
         taps = fir_taps("hp9", 1e-7 * N ** 3) if kind == "sphere" else fir_taps("none")
         return {"name": name, "N": N, "eps_r": geom, "pulse": pulse(N, eps), "taps": taps,
                 "steps": 256}
+    if name.startswith("box"):
+        # "boxWxVxU": an eps_r = 12 block filling a W x V x U grid (u fastest), hp9 FIR,
+        # plane wave along +u; small anisotropic cases that still reach long lag windows
+        W, V, U = (int(v) for v in name[3:].split("x"))
+        M = W * V * U
+        return {"name": name, "N": max(W, V, U), "eps_r": np.full((W, V, U), 12.0),
+                "pulse": pulse(0, 12.0, k_hat=(1.0, 0.0, 0.0), p_hat=(0.0, 1.0, 0.0)),
+                "taps": fir_taps("hp9", 1e-7 * M), "steps": 256}
     raise ValueError(name)
