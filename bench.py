@@ -2,11 +2,11 @@
 
 Workload (default): dielectric sphere eps_r = 12 voxelised in a 104^3 grid
 (1,124,864 voxels of the bounding grid, 589,344 inside, 3 components), c dt = h,
-9-tap linear-phase high-pass FIR regularisation with delta = 1e-7 * 104^3, single
-x-polarised +z modulated-Gaussian plane wave (the pulse peaks inside the timed window).
+FIR3 regularisation (Eq. FIR3) with delta = 1e-7 * 104^3, single x-polarised +z
+modulated-Gaussian plane wave (the pulse peaks inside the timed window).
 
-Variants: FP32-history and FP64 with the blocked temporal scheme (block B = 16, levels
-16..128), and the plain FP64 direct march for comparison.  A bench "step" is one pass
+Variants: FP32-history and FP64 with the blocked temporal scheme (block B = 8, levels
+8..128), and the plain FP64 direct march for comparison.  A bench "step" is one pass
 of every row of the hot path: for the blocked scheme one period of the block schedule
 (S_max = 128 time steps, in which every level fires), for the direct scheme one time
 step.  Each time step runs the forward FFT of J_{n-1}, the far-lag block products due
@@ -319,7 +319,7 @@ def run_ours(args, rank, world):
 
 def oracle_sample(steps, warmup):
     """The CPU oracle's direct-sum march (Eqs. PnMOT + dense LU solve) on a bounded
-    sample of the workload: the same sphere (eps_r = 12, hp9 FIR, plane wave) at
+    sample of the workload: the same sphere (eps_r = 12, FIR3, plane wave) at
     10^3 voxels; table and factorisation are setup and not timed."""
     from oracle import excitation, kernel_table, march
     from oracle.spline import num_lags
@@ -339,7 +339,7 @@ def oracle_sample(steps, warmup):
         cores = os.cpu_count()
     return {"value": eps.size * steps / sec, "unit": "voxel-timesteps/s", "cores": cores,
             "kind": "oracle",
-            "sample": "direct-sum oracle march, sphere eps_r=12 in a %d^3 grid (hp9 FIR), "
+            "sample": "direct-sum oracle march, sphere eps_r=12 in a %d^3 grid (FIR3), "
                       "%d steps (element table and LU setup untimed)" % (N, steps)}
 
 
@@ -382,7 +382,7 @@ def main():
         "dtype": "f32 history (FFT, spectra, lag products, inner CG) + double-float CG "
                  "residual + f64 (elements, FIR, state J)" if prec == "fp32_history" else "f64",
         "data": "synthetic",
-        "config": {"workload": "sphere eps_r=12, %d^3 voxels (%d), c dt = h, hp9 FIR "
+        "config": {"workload": "sphere eps_r=12, %d^3 voxels (%d), c dt = h, FIR3 "
                                "delta=1e-7*M, +z x-polarised modulated Gaussian plane wave"
                                % (round(M ** (1 / 3)), M),
                    "variant": head_key,

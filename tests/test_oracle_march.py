@@ -119,7 +119,9 @@ def test_pdsa_binomials_and_fir_identity():
 
 
 def test_fir_taps_against_paper():
-    """Eqs. FIR2-FIR4 as printed (FIR4 last tap per reading R7) and Eq. RegReq1."""
+    """Eqs. FIR2-FIR4 as printed (FIR4 last tap per reading R7), Eq. RegReq1, and the
+    magnitude (Eq. FIRmagnitude) of the 9-tap binomial member of the family in closed
+    form, delta sin^8(theta / 2)."""
     rows = {}
     for line in open(os.path.join(GOLDEN, "fir_taps_paper.txt")):
         if line.strip() and not line.startswith("#"):
@@ -129,6 +131,12 @@ def test_fir_taps_against_paper():
         taps = wl.fir_taps(k, 1.0)
         assert np.array_equal(taps, rows[k])
         assert abs(np.sum(taps * (-1.0) ** np.arange(len(taps))) - 1.0) < 1e-15
+    b = wl.fir_taps("binom9", 0.1125)                # the FIR2/FIR3 family at 9 taps
+    assert abs(np.sum(b * (-1.0) ** np.arange(9)) - 0.1125) < 1e-15
+    th = np.linspace(0.0, np.pi, 7)
+    mag = np.abs(np.exp(-1j * np.outer(th, np.arange(9))) @ b)   # Eq. FIRmagnitude
+    assert np.abs(mag - 0.1125 * np.sin(th / 2) ** 8).max() < 1e-15
+    assert np.abs(b - b[::-1]).max() == 0.0
     h = wl.fir_taps("hp9", 0.1125)
     assert abs(np.sum(h * (-1.0) ** np.arange(9)) - 0.1125) < 1e-15
     assert np.abs(h - h[::-1]).max() < 1e-15          # type-I linear phase

@@ -102,6 +102,12 @@ def fir_taps(kind, delta=0.0):
     'hp9'        9-tap type-I linear-phase high-pass, windowed sinc with a Hamming
                  window and cutoff 0.05 of the sampling rate, h = unit impulse at
                  n = 4 minus the low-pass, scaled so sum (-1)^n delta_n = delta.
+    'binom9'     9-tap linear-phase high-pass of the family of FIR2 and FIR3,
+                 delta / 2^8 (1 - z^-1)^8: meets sum (-1)^n delta_n = delta and has the
+                 smallest magnitude near theta = 0 (delta sin^8(theta / 2)).
+    The two 9-tap filters are kept for experiments; with delta = 1e-7 M they leave
+    the eps_r = 12 sphere marches unstable (hp9 from 32^3, binom9 at 104^3), while
+    FIR3 keeps them bounded, so the named workloads use FIR3.
     """
     if kind == "none":
         return np.zeros(0)
@@ -111,6 +117,8 @@ def fir_taps(kind, delta=0.0):
         return np.array([0.25, -0.5, 0.25]) * delta
     if kind == "fir4":
         return np.array([1.0, -3.0, 3.0, -1.0]) / 8.0 * delta
+    if kind == "binom9":
+        return np.array([math.comb(8, n) * (-1.0) ** n for n in range(9)]) / 256.0 * delta
     if kind == "hp9":
         n = np.arange(9) - 4.0
         fc = 0.05
@@ -137,7 +145,7 @@ def config(name):
         N = 32
         delta = 1e-7 * N ** 3
         return {"name": "sphere32", "N": N, "eps_r": sphere(N, 12.0), "pulse": pulse(N, 12.0),
-                "taps": fir_taps("hp9", delta), "steps": 2048}
+                "taps": fir_taps("fir3", delta), "steps": 2048}
     if name == "block48":
         N = 48
         return {"name": "block48", "N": N, "eps_r": heterogeneous_block(N),
@@ -146,22 +154,22 @@ def config(name):
         N = 104
         delta = 1e-7 * N ** 3
         return {"name": "sphere104", "N": N, "eps_r": sphere(N, 12.0), "pulse": pulse(N, 12.0),
-                "taps": fir_taps("hp9", delta), "steps": 4096}
+                "taps": fir_taps("fir3", delta), "steps": 4096}
     if name.startswith("sphere") or name.startswith("cube"):
-        # small variants used by tests, e.g. "sphere10" (FIR hp9) or "cube6"
+        # small variants used by tests, e.g. "sphere10" (FIR3) or "cube6"
         kind = "sphere" if name.startswith("sphere") else "cube"
         N = int(name[len(kind):])
         eps = 12.0 if kind == "sphere" else 4.0
         geom = sphere(N, eps) if kind == "sphere" else cube(N, eps)
-        taps = fir_taps("hp9", 1e-7 * N ** 3) if kind == "sphere" else fir_taps("none")
+        taps = fir_taps("fir3", 1e-7 * N ** 3) if kind == "sphere" else fir_taps("none")
         return {"name": name, "N": N, "eps_r": geom, "pulse": pulse(N, eps), "taps": taps,
                 "steps": 256}
     if name.startswith("box"):
-        # "boxWxVxU": an eps_r = 12 block filling a W x V x U grid (u fastest), hp9 FIR,
+        # "boxWxVxU": an eps_r = 12 block filling a W x V x U grid (u fastest), FIR3,
         # plane wave along +u; small anisotropic cases that still reach long lag windows
         W, V, U = (int(v) for v in name[3:].split("x"))
         M = W * V * U
         return {"name": name, "N": max(W, V, U), "eps_r": np.full((W, V, U), 12.0),
                 "pulse": pulse(0, 12.0, k_hat=(1.0, 0.0, 0.0), p_hat=(0.0, 1.0, 0.0)),
-                "taps": fir_taps("hp9", 1e-7 * M), "steps": 256}
+                "taps": fir_taps("fir3", 1e-7 * M), "steps": 256}
     raise ValueError(name)
