@@ -183,6 +183,45 @@ mot_status mot_adjoint(mot_ctx* ctx, int n_steps, const double* J, const double*
                        double* grad_eps, double* lambda, void* stream);
 
 /*
+ * The adjoint march in segments (checkpointed gradients).  mot_adjoint is one segment
+ * of these.  Row m of the gradient at step n reads J_{n-l,m} for l < L = max(taps, 2)
+ * only, so a segment needs the currents of its own steps and L - 1 before them, which
+ * the caller may recompute from a checkpoint (mot_restart) instead of keeping all N.
+ *
+ * mot_adjoint_begin - open an adjoint run of N = n_total forward steps on the context
+ *   (resets the march state; mot_march / mot_eval_history / mot_restart are refused
+ *   until mot_adjoint_end).
+ * mot_adjoint_run - advance by n_count adjoint steps: forward steps n_hi down to
+ *   n_lo = n_hi - n_count + 1, where n_hi = N - (adjoint steps done so far).
+ *  J_win      [win_count][M][3] currents J_{win_first} .. (host or device); must cover
+ *             steps max(1, n_lo - L + 1) .. n_hi
+ *  dO_dJ      [n_count][M][3] g_n for n = n_lo .. n_hi (host or device)
+ *  lambda     [n_count][M][3] optional output of lambda_{n_lo} .. lambda_{n_hi}, or NULL
+ * mot_adjoint_end - close the run; with grad_eps non-NULL (all N steps done) write
+ *   dO/deps [M] (host or device) as for mot_adjoint; NULL abandons the run.
+ * Errors: MOT_ERR_ARG (no open run, coverage, steps left), MOT_ERR_OOM,
+ * MOT_ERR_NOT_CONVERGED / MOT_ERR_UNSTABLE (the run stays open), MOT_ERR_CUDA.
+ */
+mot_status mot_adjoint_begin(mot_ctx* ctx, int n_total, void* stream);
+mot_status mot_adjoint_run(mot_ctx* ctx, int n_count, const double* J_win, int win_first,
+                           int win_count, const double* dO_dJ, double* lambda, void* stream);
+mot_status mot_adjoint_end(mot_ctx* ctx, double* grad_eps, void* stream);
+
+/*
+ * mot_restart - continue a march from a saved history: afterwards the next mot_march
+ * step is n0 + 1, exactly as if J_1 .. J_n0 had been marched (the history sum of
+ * Eq. PnMOT reaches back ell steps, so the last ell currents determine every later
+ * step; the spectral ring and the far-level accumulators are rebuilt by replaying the
+ * history path over them).
+ *  n0      steps already marched (>= 0; 0 restarts from rest)
+ *  n_hist  currents given, min(n0, ell) <= n_hist <= n0
+ *  J_hist  [n_hist][M][3] J_{n0-n_hist+1} .. J_n0 (host or device)
+ * Staged excitation is cleared (stage E_{n0+1}.. with mot_set_excitation).
+ * Errors: MOT_ERR_ARG, MOT_ERR_OOM, MOT_ERR_CUDA.
+ */
+mot_status mot_restart(mot_ctx* ctx, int n0, int n_hist, const double* J_hist, void* stream);
+
+/*
  * mot_get_table - copy interaction elements G_l^{ab}(d) of lags l0..l0+n_lags-1 on
  * the octant d in [0,U-1]x[0,V-1]x[0,W-1] to host memory.
  *  out  host pointer, [n_lags][6][W][V][U] doubles, component order xx, yy, zz,

@@ -58,6 +58,8 @@ mot_status guarded(mot_ctx* c, F&& f) {
 template <typename R> void alloc_history(mot_ctx* c) { mot::history_alloc<R>(c); }
 
 void free_all(mot_ctx* c) {
+    cudaFree(c->adj_gchi);
+    c->adj_gchi = nullptr;
     for (int a = 0; a < 3; ++a) mot::fft_free_axis(c->ax[a]);
     for (int k = 0; k < 8; ++k) mot::fft_free_axis(c->lev_fft[k]);
     mot::history_free<double>(c);
@@ -341,6 +343,7 @@ mot_status mot_plane_wave(mot_ctx* c, const double k_hat[3], const double p_hat[
 
 mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
     if (!c) return MOT_ERR_ARG;
+    if (c->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
     if (n_steps < 1) { c->err = "n_steps must be >= 1"; return MOT_ERR_ARG; }
     mot_status result = MOT_OK;
     mot_status st = guarded(c, [&] {
@@ -435,6 +438,7 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
 mot_status mot_eval_history(mot_ctx* c, int n_hist, const double* J_hist, double* P_out,
                             void* stream) {
     if (!c) return MOT_ERR_ARG;
+    if (c->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
     if (n_hist < 1 || n_hist > c->ell || !J_hist || !P_out) {
         c->err = "n_hist must be in 1..ell and buffers non-null";
         return MOT_ERR_ARG;
@@ -472,11 +476,88 @@ mot_status mot_eval_history(mot_ctx* c, int n_hist, const double* J_hist, double
     });
 }
 
-mot_status mot_adjoint(mot_ctx* c, int n_steps, const double* J, const double* dO_dJ,
-                       double* grad_eps, double* lambda, void* stream) {
+namespace {
+
+// stage `count` steps of an AoS host or device array on the device (owned copy if host)
+const double* on_device(mot_ctx* c, const double* src, long long count,
+                        std::vector<void*>& owned, cudaStream_t s) {
+    if (is_device_ptr(src)) return src;
+    double* d = nullptr;
+    const long long bytes = sizeof(double) * 3 * c->M * count;
+    MOT_CUDA_TRY(cudaMalloc(&d, bytes));
+    owned.push_back(d);
+    MOT_CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+    return d;
+}
+
+void adjoint_release(mot_ctx* c) {
+    cudaFree(c->adj_gchi);
+    c->adj_gchi = nullptr;
+    c->adj_total = 0;
+    c->adj_done = 0;
+    c->adjoint = false;
+}
+
+}  // namespace
+
+mot_status mot_restart(mot_ctx* c, int n0, int n_hist, const double* J_hist, void* stream) {
     if (!c) return MOT_ERR_ARG;
-    if (n_steps < 1 || !J || !dO_dJ || !grad_eps) {
-        c->err = "n_steps >= 1 and J, dO_dJ, grad_eps non-null required";
+    if (c->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
+    if (n0 < 0 || n_hist < std::min(n0, c->ell) || n_hist > n0 || (n_hist > 0 && !J_hist)) {
+        c->err = "mot_restart needs min(n0, ell) <= n_hist <= n0 currents J_{n0-n_hist+1..n0}";
+        return MOT_ERR_ARG;
+    }
+    std::vector<void*> owned;
+    mot_status st = guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        reset_state(c, s);
+        const double* Jd = n_hist ? on_device(c, J_hist, n_hist, owned, s) : nullptr;
+        const long long step = 3 * c->M;
+        // replay the history path over the window: every far-level firing that
+        // contributes to a time after n0 happens inside it, and currents older than ell
+        // steps contribute to no later time
+        const int t0 = n0 - n_hist + 1;
+        for (int t = t0; t <= n0; ++t) {
+            mot::read_aos(c, Jd + (long long)(t - t0) * step,
+                          c->J + mot::slot_index(t, c->jring) * step, s);
+            if (t < n0) history_for(c, t + 1, s);
+        }
+        c->n_done = n0;
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+    for (void* p : owned) cudaFree(p);
+    return st;
+}
+
+mot_status mot_adjoint_begin(mot_ctx* c, int n_total, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_total < 1) { c->err = "n_total must be >= 1"; return MOT_ERR_ARG; }
+    if (c->adj_total) { c->err = "an adjoint run is already open"; return MOT_ERR_ARG; }
+    const mot_status st = guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        MOT_CUDA_TRY(cudaMalloc(&c->adj_gchi, sizeof(double) * c->M));
+        MOT_CUDA_TRY(cudaMemsetAsync(c->adj_gchi, 0, sizeof(double) * c->M, s));
+        reset_state(c, s);
+        c->adjoint = true;
+        c->adj_total = n_total;
+        c->adj_done = 0;
+        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+    if (st != MOT_OK) adjoint_release(c);
+    return st;
+}
+
+mot_status mot_adjoint_run(mot_ctx* c, int n_count, const double* J_win, int win_first,
+                           int win_count, const double* dO_dJ, double* lambda, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (!c->adj_total) { c->err = "no adjoint run open (mot_adjoint_begin first)"; return MOT_ERR_ARG; }
+    const int n_hi = c->adj_total - c->adj_done, n_lo = n_hi - n_count + 1;
+    const int L = std::max(c->n_taps, 2);
+    if (n_count < 1 || n_lo < 1 || !J_win || !dO_dJ ||
+        win_first > std::max(1, n_lo - L + 1) || win_first + win_count - 1 < n_hi) {
+        c->err = "adjoint run: need 1 <= n_count <= steps left and currents covering steps "
+                 "max(1, n_lo - L + 1) .. n_hi (L = max(taps, 2))";
         return MOT_ERR_ARG;
     }
     mot_status result = MOT_OK;
@@ -484,63 +565,40 @@ mot_status mot_adjoint(mot_ctx* c, int n_steps, const double* J, const double* d
     mot_status st = guarded(c, [&] {
         cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
         const long long step = 3 * c->M;
-        const long long bytes = sizeof(double) * step * n_steps;
-        auto device_copy = [&](const double* src) -> const double* {
-            if (is_device_ptr(src)) return src;
-            double* d = nullptr;
-            MOT_CUDA_TRY(cudaMalloc(&d, bytes));
-            owned.push_back(d);
-            MOT_CUDA_TRY(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
-            return d;
-        };
-        const double* Jd = device_copy(J);
-        const double* gd = device_copy(dO_dJ);
+        const double* Jd = on_device(c, J_win, win_count, owned, s);
+        const double* gd = on_device(c, dO_dJ, n_count, owned, s);
         double* lamd = nullptr;
         if (lambda) {
             if (is_device_ptr(lambda)) {
                 lamd = lambda;
             } else {
-                MOT_CUDA_TRY(cudaMalloc(&lamd, bytes));
+                MOT_CUDA_TRY(cudaMalloc(&lamd, sizeof(double) * step * n_count));
                 owned.push_back(lamd);
             }
         }
-        double* gchi = nullptr;
-        MOT_CUDA_TRY(cudaMalloc(&gchi, sizeof(double) * c->M));
-        owned.push_back(gchi);
-        MOT_CUDA_TRY(cudaMemsetAsync(gchi, 0, sizeof(double) * c->M, s));
-        if (n_steps > c->norms_cap) {
+        if (n_count > c->norms_cap) {
             MOT_CUDA_TRY(cudaStreamSynchronize(s));
             cudaFree(c->norms);
             c->norms = nullptr;
             c->norms_cap = 0;
-            MOT_CUDA_TRY(cudaMalloc(&c->norms, sizeof(double) * n_steps));
-            c->norms_cap = n_steps;
+            MOT_CUDA_TRY(cudaMalloc(&c->norms, sizeof(double) * n_count));
+            c->norms_cap = n_count;
         }
-        reset_state(c, s);
-        c->adjoint = true;
-        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
-        for (int tau = 1; tau <= n_steps; ++tau) {
-            const int n = n_steps + 1 - tau;
+        for (int i = 0; i < n_count; ++i) {
+            const int tau = c->adj_done + 1 + i;
+            const int n = c->adj_total + 1 - tau;
             history_for(c, tau, s);
-            mot::adjoint_step(c, tau, n, gd + (long long)(n - 1) * step, Jd, gchi,
-                              lamd ? lamd + (long long)(n - 1) * step : nullptr,
-                              c->norms + tau - 1, s);
+            mot::adjoint_step(c, tau, n, gd + (long long)(n - n_lo) * step, Jd, win_first,
+                              c->adj_gchi, lamd ? lamd + (long long)(n - n_lo) * step : nullptr,
+                              c->norms + i, s);
         }
-        std::vector<double> g(c->M), e(c->M);
         int hs[4];
-        MOT_CUDA_TRY(cudaMemcpyAsync(g.data(), gchi, sizeof(double) * c->M, cudaMemcpyDeviceToHost, s));
-        MOT_CUDA_TRY(cudaMemcpyAsync(e.data(), c->eps, sizeof(double) * c->M, cudaMemcpyDeviceToHost, s));
         MOT_CUDA_TRY(cudaMemcpyAsync(hs, c->dstatus, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
         if (lambda && lamd != lambda)
-            MOT_CUDA_TRY(cudaMemcpyAsync(lambda, lamd, bytes, cudaMemcpyDeviceToHost, s));
+            MOT_CUDA_TRY(cudaMemcpyAsync(lambda, lamd, sizeof(double) * step * n_count,
+                                         cudaMemcpyDeviceToHost, s));
         MOT_CUDA_TRY(cudaStreamSynchronize(s));
-        for (long long m = 0; m < c->M; ++m) g[m] /= e[m] * e[m];
-        MOT_CUDA_TRY(cudaMemcpy(grad_eps, g.data(), sizeof(double) * c->M,
-                                is_device_ptr(grad_eps) ? cudaMemcpyHostToDevice
-                                                        : cudaMemcpyHostToHost));
-        c->adjoint = false;
-        reset_state(c, s);
-        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+        c->adj_done += n_count;
         if (hs[1] & 1) {
             result = MOT_ERR_NOT_CONVERGED;
             c->err = "adjoint: CG did not converge";
@@ -550,8 +608,57 @@ mot_status mot_adjoint(mot_ctx* c, int n_steps, const double* J, const double* d
         }
     });
     for (void* p : owned) cudaFree(p);
-    c->adjoint = false;
     return st != MOT_OK ? st : result;
+}
+
+mot_status mot_adjoint_end(mot_ctx* c, double* grad_eps, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (!c->adj_total) { c->err = "no adjoint run open"; return MOT_ERR_ARG; }
+    if (grad_eps && c->adj_done != c->adj_total) {
+        c->err = "adjoint run incomplete: steps left";
+        return MOT_ERR_ARG;
+    }
+    mot_status st = guarded(c, [&] {
+        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        if (grad_eps) {
+            std::vector<double> g(c->M), e(c->M);
+            MOT_CUDA_TRY(cudaMemcpyAsync(g.data(), c->adj_gchi, sizeof(double) * c->M,
+                                         cudaMemcpyDeviceToHost, s));
+            MOT_CUDA_TRY(cudaMemcpyAsync(e.data(), c->eps, sizeof(double) * c->M,
+                                         cudaMemcpyDeviceToHost, s));
+            MOT_CUDA_TRY(cudaStreamSynchronize(s));
+            for (long long m = 0; m < c->M; ++m) g[m] /= e[m] * e[m];   // dchi/deps = 1/eps^2
+            MOT_CUDA_TRY(cudaMemcpy(grad_eps, g.data(), sizeof(double) * c->M,
+                                    is_device_ptr(grad_eps) ? cudaMemcpyHostToDevice
+                                                            : cudaMemcpyHostToHost));
+        }
+        c->adjoint = false;
+        reset_state(c, s);
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+    });
+    adjoint_release(c);
+    return st;
+}
+
+mot_status mot_adjoint(mot_ctx* c, int n_steps, const double* J, const double* dO_dJ,
+                       double* grad_eps, double* lambda, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_steps < 1 || !J || !dO_dJ || !grad_eps) {
+        c->err = "n_steps >= 1 and J, dO_dJ, grad_eps non-null required";
+        return MOT_ERR_ARG;
+    }
+    mot_status st = mot_adjoint_begin(c, n_steps, stream);
+    if (st != MOT_OK) return st;
+    const mot_status run = mot_adjoint_run(c, n_steps, J, 1, n_steps, dO_dJ, lambda, stream);
+    if (run != MOT_OK && run != MOT_ERR_NOT_CONVERGED && run != MOT_ERR_UNSTABLE) {
+        mot_adjoint_end(c, nullptr, stream);
+        return run;
+    }
+    const std::string keep = c->err;
+    st = mot_adjoint_end(c, grad_eps, stream);
+    if (st != MOT_OK) return st;
+    if (run != MOT_OK) c->err = keep;
+    return run;
 }
 
 mot_status mot_get_table(mot_ctx* c, int l0, int n_lags, double* out) {

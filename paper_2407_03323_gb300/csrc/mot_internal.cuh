@@ -139,6 +139,9 @@ struct mot_ctx {
     long long smax = 1;          // accumulator slots of all levels (sum of S)
 
     bool adjoint = false;        // rings hold lambda; the FFT input is chi * lambda
+    int adj_total = 0;           // segmented adjoint: forward steps N of the run
+    int adj_done = 0;            //   adjoint steps done (tau)
+    double* adj_gchi = nullptr;  //   dO/dchi accumulated so far (device, [M])
 
     // counters and optional phase timing
     mot_stats stats = {};
@@ -191,7 +194,8 @@ void write_aos(mot_ctx* c, int n, double* out_dev, cudaStream_t s);
 void read_aos(mot_ctx* c, const double* in_dev, double* slot, cudaStream_t s);
 void history_out(mot_ctx* c, int n, double* out_dev, cudaStream_t s);
 void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double* J_aos,
-                  double* grad_chi, double* lam_out, double* norm2_out, cudaStream_t s);
+                  int j_first, double* grad_chi, double* lam_out, double* norm2_out,
+                  cudaStream_t s);
 // excitation.cu
 void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, double st,
                 double t0, int n_first, int n_steps, double* Edev, cudaStream_t s);

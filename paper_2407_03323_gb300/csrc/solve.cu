@@ -678,7 +678,7 @@ __global__ void k_adj_vacuum(long long M, int U, int V, int W, const double* __r
 
 __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __restrict__ Ln,
                            const double* __restrict__ lam_vac, const double* __restrict__ J,
-                           int n, int n_taps, double* __restrict__ grad_chi,
+                           int j_first, int n, int n_taps, double* __restrict__ grad_chi,
                            double* __restrict__ lam_out) {
     const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
@@ -690,9 +690,9 @@ __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __
             lam = Ln[beta * M + m] * ichi;
             double q = 0.0;
             const int L = n_taps > 2 ? n_taps : 2;
-            for (int l = 0; l < L && n - l >= 1; ++l) {
+            for (int l = 0; l < L && n - l >= 1; ++l) {   // J[0] holds step j_first
                 const double w = (l < 2 ? 0.5 : 0.0) + (l < n_taps ? c_taps[l] : 0.0);
-                q += w * J[((long long)(n - l - 1) * M + m) * 3 + beta];
+                q += w * J[((long long)(n - l - j_first) * M + m) * 3 + beta];
             }
             gsum += lam * q * ichi;
         } else {
@@ -1031,7 +1031,8 @@ void history_out(mot_ctx* c, int n, double* out_dev, cudaStream_t s) {
 
 // one adjoint step: tau = adjoint time (ring index), n = N + 1 - tau (forward time)
 void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double* J_aos,
-                  double* grad_chi, double* lam_out, double* norm2_out, cudaStream_t s) {
+                  int j_first, double* grad_chi, double* lam_out, double* norm2_out,
+                  cudaStream_t s) {
     const long long tot = 3 * c->M;
     const int s0 = (int)slot_index(tau, c->jring);
     if (c->precision == MOT_FP64)
@@ -1048,8 +1049,9 @@ void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double*
     k_adj_vacuum<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->U, c->V, c->W, c->vfac, mu,
                                                            c->rhs, c->cg_q);
     MOT_LAUNCH_CHECK();
-    k_adj_post<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->vfac, mu, c->cg_q, J_aos, n,
-                                                         c->n_taps, grad_chi, lam_out);
+    k_adj_post<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->vfac, mu, c->cg_q, J_aos,
+                                                         j_first, n, c->n_taps, grad_chi,
+                                                         lam_out);
     MOT_LAUNCH_CHECK();
     c->stats.launches += 4;
 }

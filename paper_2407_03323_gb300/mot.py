@@ -26,7 +26,8 @@ PRECISIONS = {"fp64": 0, "fp32_history": 1}
 SCHEMES = {"direct": 0, "blocked": 1}
 
 EXPORTS = ["mot_create", "mot_destroy", "mot_set_excitation", "mot_plane_wave",
-           "mot_plane_wave_static", "mot_march",
+           "mot_plane_wave_static", "mot_march", "mot_restart", "mot_adjoint_begin",
+           "mot_adjoint_run", "mot_adjoint_end",
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_last_error"]
 
@@ -69,6 +70,10 @@ def load_library(path=LIB_PATH):
     lib.mot_march.argtypes = [P, I, P, P]
     lib.mot_eval_history.argtypes = [P, I, P, P, P]
     lib.mot_adjoint.argtypes = [P, I, P, P, P, P, P]
+    lib.mot_adjoint_begin.argtypes = [P, I, P]
+    lib.mot_adjoint_run.argtypes = [P, I, P, I, I, P, P, P]
+    lib.mot_adjoint_end.argtypes = [P, P, P]
+    lib.mot_restart.argtypes = [P, I, I, P, P]
     lib.mot_get_table.argtypes = [P, I, I, P]
     lib.mot_get_spectrum.argtypes = [P, I, P]
     lib.mot_get_info.argtypes = [P, P, P, P, P, P, P]
@@ -220,6 +225,36 @@ class Context:
         self._check(self._lib.mot_adjoint(self._h, n, _ptr(J), _ptr(dO_dJ), grad.ctypes.data,
                                           _ptr(lam), _stream(stream)))
         return (grad, lam) if want_lambda else grad
+
+    def adjoint_begin(self, n_total, stream=None):
+        """Open a segmented adjoint run of n_total forward steps (mot_adjoint_begin)."""
+        self._check(self._lib.mot_adjoint_begin(self._h, n_total, _stream(stream)))
+
+    def adjoint_run(self, n_count, J_win, win_first, dO_dJ, want_lambda=False, stream=None):
+        """Advance the open adjoint run by n_count steps (mot_adjoint_run); J_win holds
+        J_{win_first} .., dO_dJ the g_n of the n_count forward steps, oldest first."""
+        if isinstance(J_win, np.ndarray):
+            J_win = np.ascontiguousarray(J_win, dtype=np.float64)
+        if isinstance(dO_dJ, np.ndarray):
+            dO_dJ = np.ascontiguousarray(dO_dJ, dtype=np.float64)
+        lam = np.zeros((n_count, self.M, 3)) if want_lambda else None
+        self._check(self._lib.mot_adjoint_run(self._h, n_count, _ptr(J_win), win_first,
+                                              J_win.shape[0], _ptr(dO_dJ), _ptr(lam),
+                                              _stream(stream)))
+        return lam
+
+    def adjoint_end(self, want_grad=True, stream=None):
+        """Close the adjoint run (mot_adjoint_end); returns dO/d eps_r [W][V][U]."""
+        grad = np.zeros(self.shape) if want_grad else None
+        self._check(self._lib.mot_adjoint_end(self._h, _ptr(grad), _stream(stream)))
+        return grad
+
+    def restart(self, n0, J_hist, stream=None):
+        """Continue from a saved history (mot_restart): J_hist holds J_{n0-k+1} .. J_n0."""
+        if isinstance(J_hist, np.ndarray):
+            J_hist = np.ascontiguousarray(J_hist, dtype=np.float64)
+        k = 0 if J_hist is None else J_hist.shape[0]
+        self._check(self._lib.mot_restart(self._h, n0, k, _ptr(J_hist), _stream(stream)))
 
     def eval_history(self, J_hist, out=None, stream=None):
         J = J_hist
