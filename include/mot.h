@@ -50,7 +50,8 @@ typedef enum {
     MOT_FP64 = 0,          /* every stage in FP64                                    */
     MOT_FP32_HISTORY = 1   /* FFTs, spectra and lag MAC in FP32 with compensated
                               accumulation; element quadrature, Z_0, FIR state and
-                              the CG solve stay FP64                                 */
+                              the solution J stay FP64; the CG residual is formed in
+                              double-float (float pairs, ~48 bits)                  */
 } mot_precision;
 
 typedef enum {
@@ -65,8 +66,10 @@ typedef enum {
  *
  * Computes ell (Eq. Ell), chi_m = (eps_m - 1)/eps_m (Eq. TDJVIE), the interaction
  * elements G_l(d) = K^face_l(d) - delta_ab K^vol_l(d) for lags 0..ell by FP64
- * quadrature on the GPU (Eq. Z; the element integrals are written out in
- * the design doc), their zero-padded spatial spectra (App. A), and allocates the rings.
+ * quadrature on the GPU (Eq. Z; K^vol_l = int C_d T''(l - r)/(4 pi r),
+ * K^face_l^ab = int (d_a d_b C_d) T(l - r)/(4 pi r), C_d the autocorrelation of two
+ * voxels at offset d, T the quadratic B-spline basis), their zero-padded spatial
+ * spectra (App. A), and allocates the rings.
  *
  *  grid[3]   U, V, W voxels along x, y, z (each >= 1)
  *  h[3]      voxel edges; must be equal
@@ -84,6 +87,18 @@ typedef enum {
 mot_status mot_create(const int grid[3], const double h[3], double dt,
                       const double* eps_r, const double* fir_taps, int n_taps,
                       int precision, int scheme, int block, mot_ctx** out);
+
+/*
+ * mot_create_shared - a second, independent marching state on the setup of `src`:
+ * the same grid, eps_r, FIR taps, precision, history scheme and solver settings, with
+ * the element table, kernel and level spectra, geometry and solver setup shared
+ * read-only (not recomputed, not copied).  For several excitations of one scatterer
+ * marched side by side (each context has its own stream, rings and solver vectors).
+ * `src` (or the context it shares from) must outlive every context shared from it.
+ *  out   receives the new context (NULL on error; mot_last_error(NULL) explains)
+ * Errors: MOT_ERR_ARG, MOT_ERR_STATE (src unusable), MOT_ERR_OOM, MOT_ERR_CUDA.
+ */
+mot_status mot_create_shared(mot_ctx* src, mot_ctx** out);
 
 /* Release every device and host resource of the context.  NULL is a no-op. */
 void mot_destroy(mot_ctx* ctx);

@@ -60,6 +60,19 @@ template <typename R> void alloc_history(mot_ctx* c) { mot::history_alloc<R>(c);
 void free_all(mot_ctx* c) {
     cudaFree(c->adj_gchi);
     c->adj_gchi = nullptr;
+    if (c->shared_src) {   // borrowed setup: release the references, free the state only
+        for (int a = 0; a < 3; ++a) c->ax[a] = AxisFFT();
+        for (int k = 0; k < 8; ++k) c->lev_fft[k] = AxisFFT();
+        c->eps = c->chi = c->cg_diag = c->tab = nullptr;
+        c->vfac = nullptr;
+        c->tab_l0 = nullptr;
+        c->active = c->nmask = c->tiles = nullptr;
+        c->diag32 = nullptr;
+        c->h64.ghat = nullptr; c->h64.level_spec = nullptr;
+        c->h32.ghat = nullptr; c->h32.level_spec = nullptr;
+        c->shared_src->n_shared -= 1;
+        c->shared_src = nullptr;
+    }
     for (int a = 0; a < 3; ++a) mot::fft_free_axis(c->ax[a]);
     for (int k = 0; k < 8; ++k) mot::fft_free_axis(c->lev_fft[k]);
     mot::history_free<double>(c);
@@ -289,6 +302,74 @@ void mot_destroy(mot_ctx* c) {
     cudaDeviceSynchronize();
     free_all(c);
     delete c;
+}
+
+mot_status mot_create_shared(mot_ctx* src, mot_ctx** out) {
+    if (!out) return MOT_ERR_ARG;
+    *out = nullptr;
+    if (!src) { g_create_error = "source context is NULL"; return MOT_ERR_ARG; }
+    if (src->broken) return MOT_ERR_STATE;
+    if (src->shared_src) { src = src->shared_src; }   // share the owner of the setup
+    mot_ctx* c = new mot_ctx();
+    // grid, discretisation and solver setup (values), shared device setup (pointers)
+    c->U = src->U; c->V = src->V; c->W = src->W; c->M = src->M; c->ell = src->ell;
+    for (int a = 0; a < 3; ++a) c->ax[a] = src->ax[a];
+    c->Hu = src->Hu; c->Hv = src->Hv; c->Hw = src->Hw;
+    c->nbins = src->nbins; c->noct = src->noct;
+    c->precision = src->precision; c->scheme = src->scheme; c->block = src->block;
+    c->n_taps = src->n_taps; c->taps = src->taps;
+    c->tol = src->tol; c->max_iter = src->max_iter; c->growth = src->growth;
+    c->jring = src->jring; c->hring = src->hring;
+    c->eps = src->eps; c->chi = src->chi; c->cg_diag = src->cg_diag;
+    c->active = src->active; c->nmask = src->nmask; c->tiles = src->tiles;
+    c->ntiles = src->ntiles; c->nact = src->nact;
+    c->diag32 = src->diag32; c->vfac = src->vfac;
+    c->cheb_lmin = src->cheb_lmin; c->cheb_lmax = src->cheb_lmax; c->cheb_n = src->cheb_n;
+    c->cheb_log_rate = src->cheb_log_rate; c->cheb_inv_theta = src->cheb_inv_theta;
+    for (int k = 0; k < 64; ++k) { c->cheb_c1[k] = src->cheb_c1[k]; c->cheb_c2[k] = src->cheb_c2[k]; }
+    for (int k = 0; k < 27 * 6; ++k) c->stencil[k] = src->stencil[k];
+    for (int e = 0; e < 27; ++e) c->noff[e] = src->noff[e];
+    c->tab_l0 = src->tab_l0; c->tab = src->tab;
+    c->nlev = src->nlev;
+    for (int k = 0; k < 8; ++k) {
+        c->lev_S[k] = src->lev_S[k]; c->lev_off[k] = src->lev_off[k];
+        c->lev_fft[k] = src->lev_fft[k]; c->lev_acc[k] = src->lev_acc[k];
+    }
+    c->smax = src->smax;
+    c->nsm = src->nsm; c->cg_blocks = src->cg_blocks;
+    c->shared_src = src;
+    src->n_shared += 1;
+    const long long M = c->M;
+    mot_status st = guarded(c, [&] {
+        MOT_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        if (c->precision == MOT_FP64) mot::history_alloc_shared<double>(c, src);
+        else mot::history_alloc_shared<float>(c, src);
+        MOT_CUDA_TRY(cudaMalloc(&c->J, sizeof(double) * 3 * M * c->jring));
+        MOT_CUDA_TRY(cudaMalloc(&c->rhs, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg_r, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg_q, sizeof(double) * 3 * M));
+        MOT_CUDA_TRY(cudaMalloc(&c->cg32, sizeof(float) * 16 * M));
+        MOT_CUDA_TRY(cudaMemset(c->cg32, 0, sizeof(float) * 16 * M));
+        if (src->cg_df) {
+            MOT_CUDA_TRY(cudaMalloc(&c->cg_df, sizeof(float) * 17 * M));
+            MOT_CUDA_TRY(cudaMemset(c->cg_df, 0, sizeof(float) * 16 * M));
+            MOT_CUDA_TRY(cudaMemcpy(c->cg_df + 16 * M, src->cg_df + 16 * M, sizeof(float) * M,
+                                    cudaMemcpyDeviceToDevice));
+        }
+        MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
+        MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
+        MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
+        reset_state(c, c->stream);
+        MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    });
+    if (st != MOT_OK) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return MOT_OK;
 }
 
 mot_status mot_set_excitation(mot_ctx* c, int n_steps, const double* E, void* stream) {

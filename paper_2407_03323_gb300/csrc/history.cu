@@ -329,6 +329,24 @@ void history_alloc(mot_ctx* c) {
     }
 }
 
+// march-state buffers of a context that shares src's kernel and level spectra
+template <typename R>
+void history_alloc_shared(mot_ctx* c, mot_ctx* src) {
+    typedef typename CT<R>::c C;
+    HistoryBuffers<R>& hb = hbuf<R>(c);
+    const HistoryBuffers<R>& sb = hbuf<R>(src);
+    const long long slot = 3 * c->nbins;
+    hb.ghat = sb.ghat;
+    hb.level_spec = sb.level_spec;
+    MOT_CUDA_TRY(cudaMalloc(&hb.jhat_ring, sizeof(C) * slot * c->hring));
+    MOT_CUDA_TRY(cudaMalloc(&hb.phat, sizeof(C) * slot));
+    MOT_CUDA_TRY(cudaMalloc(&hb.tmp1, sizeof(C) * 3LL * c->W * c->V * c->Hu));
+    MOT_CUDA_TRY(cudaMalloc(&hb.tmp2, sizeof(C) * 3LL * c->W * c->ax[1].P * c->Hu));
+    MOT_CUDA_TRY(cudaMalloc(&hb.hist_spatial, sizeof(R) * 3 * c->M));
+    if (c->scheme == MOT_HISTORY_BLOCKED)
+        MOT_CUDA_TRY(cudaMalloc(&hb.acc_ring, sizeof(C) * slot * c->smax));
+}
+
 template <typename R>
 void history_free(mot_ctx* c) {
     HistoryBuffers<R>& hb = hbuf<R>(c);
@@ -947,6 +965,8 @@ void history_step(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t* ev) {
 
 template void history_alloc<double>(mot_ctx*);
 template void history_alloc<float>(mot_ctx*);
+template void history_alloc_shared<double>(mot_ctx*, mot_ctx*);
+template void history_alloc_shared<float>(mot_ctx*, mot_ctx*);
 template void history_free<double>(mot_ctx*);
 template void history_free<float>(mot_ctx*);
 template void history_reset<double>(mot_ctx*, cudaStream_t);

@@ -120,6 +120,7 @@ struct mot_ctx {
     int fail_step = 0;
     int last_iters = 0;
     double stencil[27 * 6];      // G_0(d) for |d_i| <= 1 (host copy)
+    int noff[27] = {0};          // voxel-index offset of neighbour e (the 27-point stencil)
 
     // interaction table (sparse in lag): per octant offset, window of WIN lags
     int* tab_l0 = nullptr;       // [W*V*U]
@@ -149,6 +150,11 @@ struct mot_ctx {
     std::vector<cudaEvent_t> events;   // 6 per step of the current call
 
     cudaStream_t stream = nullptr;
+
+    // mot_create_shared: setup (geometry, table, spectra, twiddles) borrowed from
+    // shared_src, which must outlive this context; n_shared counts the borrowers
+    mot_ctx* shared_src = nullptr;
+    int n_shared = 0;
     int nsm = 0;
     int cg_blocks = 0;
     bool broken = false;
@@ -179,6 +185,7 @@ template <typename R>
 void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s);
 // history.cu
 template <typename R> void history_alloc(mot_ctx* c);
+template <typename R> void history_alloc_shared(mot_ctx* c, mot_ctx* src);
 template <typename R> void history_free(mot_ctx* c);
 // ev (optional, 3 events): recorded after the forward FFT, after the far-lag block
 // products and after the near-lag MAC

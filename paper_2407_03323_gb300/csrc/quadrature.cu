@@ -1,7 +1,10 @@
 // Interaction-element quadrature on the GPU in FP64 (Eq. Z with S of Eq. TDJVIE).
 //
 // With h = c dt = 1 and C_d(x) = L(x-dx) L(y-dy) L(z-dz) the autocorrelation of two
-// unit voxels (L the unit hat), the elements are (derivation in the design doc):
+// unit voxels (L the unit hat), the elements are (with the lag-l time dependence of
+// the retarded potential (Sec. 2.1) under the quadratic-spline basis, the curl-curl of
+// the field operator written as grad div minus a second time derivative, and the grad
+// div moved onto C_d by parts, so that it acts as a double surface integral):
 //   K^vol_l(d)      = int C_d(x) T''(l - r) / (4 pi r) dx
 //   K^face_l^ab(d)  = int (d_a d_b C_d)(x) T(l - r) / (4 pi r) dx
 //   G_l^ab(d)       = K^face_l^ab(d) - delta_ab K^vol_l(d)

@@ -29,7 +29,18 @@ constexpr int MAXTAPS = 64;
 constexpr int MAXCHEB = 64;
 
 __constant__ double c_stencil[27 * 6];   // G_0(e) for e in {-1,0,1}^3, order xx yy zz xy xz yz
-__constant__ double c_taps[MAXTAPS];
+// FIR taps delta_0 .. delta_{n-1} of a context, passed by value to the kernels that
+// read them (several contexts with different taps may be live at once)
+struct Taps {
+    double d[MAXTAPS];
+    int n;
+};
+inline Taps taps_of(const mot_ctx* c) {
+    Taps t;
+    for (int l = 0; l < MAXTAPS; ++l) t.d[l] = l < c->n_taps ? c->taps[l] : 0.0;
+    t.n = c->n_taps;
+    return t;
+}
 
 // ring slot of J_{n-l}: (s0 - l) mod jring, s0 = n mod jring, 0 <= l < jring
 __device__ __forceinline__ long long jslot(int s0, int l, int jring, long long stride) {
@@ -44,7 +55,7 @@ __device__ __forceinline__ long long jslot(int s0, int l, int jring, long long s
 template <typename R>
 __global__ void k_epilogue(long long M, const double* __restrict__ f, const double* __restrict__ En,
                            const R* __restrict__ hist, double* __restrict__ Jring, int s0,
-                           int jring, int n_taps, double* __restrict__ b) {
+                           int jring, Taps tp, double* __restrict__ b) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * M) return;
     const long long m = i % M;
@@ -55,7 +66,7 @@ __global__ void k_epilogue(long long M, const double* __restrict__ f, const doub
     const double j2 = Jring[jslot(s0, 2, jring, st) + i];
     const double j3 = Jring[jslot(s0, 3, jring, st) + i];
     double P = f[m] * j1 - f[3 * M + m] * (double)hist[i];
-    for (int l = 1; l < n_taps; ++l) P += c_taps[l] * Jring[jslot(s0, l, jring, st) + i];
+    for (int l = 1; l < tp.n; ++l) P += tp.d[l] * Jring[jslot(s0, l, jring, st) + i];
     const double rhs = e - P;
     double* Jn = Jring + jslot(s0, 0, jring, st);
     const double ichi = f[M + m];
@@ -70,6 +81,7 @@ __global__ void k_epilogue(long long M, const double* __restrict__ f, const doub
 
 struct CGArgs {
     long long M;
+    int noff[27];         // neighbour e = (ez+1)*9 + (ey+1)*3 + (ex+1): m offset ex + U ey + U V ez
     const int* act;       // active voxels (chi > 0)
     const int* nmask;     // per active voxel: bit e set if neighbour e (0..26) is in the grid
     long long nact;
@@ -106,8 +118,6 @@ struct CGArgs {
     double* norm2;        // ||x||^2 output
 };
 
-// neighbour e = (ez+1)*9 + (ey+1)*3 + (ex+1); c_noff[e] = ex + U ey + U V ez
-__constant__ int c_noff[27];
 __constant__ float c_st32[27 * 6];   // FP32 copy of c_stencil
 __constant__ float c_stl[27 * 6];    // c_stencil - c_st32 rounded to FP32 (double-float low parts)
 // the 13 neighbours e > 13 pair with their mirrors 26 - e; G_0(-e) = G_0(e)
@@ -161,7 +171,7 @@ __device__ __forceinline__ void applyA64(const CGArgs& a, const double* __restri
     const double d = a.diag[m];
     double o0 = (d - S0[0]) * x[m], o1 = (d - S0[1]) * x[M + m], o2 = (d - S0[2]) * x[2 * M + m];
     auto load = [&](auto e, double& sx, double& sy, double& sz) {
-        const int m2 = m + c_noff[decltype(e)::value];
+        const int m2 = m + a.noff[decltype(e)::value];
         sx += x[m2];
         sy += x[M + m2];
         sz += x[2 * M + m2];
@@ -265,7 +275,7 @@ __device__ __forceinline__ float4 residual_df(const CGArgs& a, int m, int mask) 
     df_msub(H0[1], L0[1], ch.y, cl.y, oh[1], ol[1]);
     df_msub(H0[2], L0[2], ch.z, cl.z, oh[2], ol[2]);
     auto load = [&](auto e, float* sh, float* sl) {
-        const int m2 = m + c_noff[decltype(e)::value];
+        const int m2 = m + a.noff[decltype(e)::value];
         const float4 vh = a.xh[m2], vl = a.xl[m2];
         df_add(sh[0], sl[0], vh.x, vl.x);
         df_add(sh[1], sl[1], vh.y, vl.y);
@@ -436,7 +446,7 @@ __device__ __forceinline__ double grid_total(const double* red, int nb) {
 // evaluated in double-float arithmetic on float-pair copies of x and b (FP32-history
 // mode); x is split at entry, corrected in pairs and merged back to FP64 at exit.
 template <bool DF>
-__global__ void __launch_bounds__(NT, 3) k_cg(CGArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) {
     cg::grid_group grid = cg::this_grid();
     const long long M = a.M;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -624,7 +634,7 @@ __global__ void k_from_aos(const double* __restrict__ in, long long M, double* _
 template <typename R>
 __global__ void k_epilogue_adj(long long M, const double* __restrict__ f,
                                const double* __restrict__ g, const R* __restrict__ hist,
-                               double* __restrict__ Lring, int s0, int jring, int n_taps,
+                               double* __restrict__ Lring, int s0, int jring, Taps tp,
                                double* __restrict__ b) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * M) return;
@@ -635,7 +645,7 @@ __global__ void k_epilogue_adj(long long M, const double* __restrict__ f,
     const double l2 = Lring[jslot(s0, 2, jring, st) + i];
     const double l3 = Lring[jslot(s0, 3, jring, st) + i];
     double P = f[m] * l1 - (double)hist[i];
-    for (int l = 1; l < n_taps; ++l) P += c_taps[l] * Lring[jslot(s0, l, jring, st) + i];
+    for (int l = 1; l < tp.n; ++l) P += tp.d[l] * Lring[jslot(s0, l, jring, st) + i];
     const double rhs = g[m * 3 + beta] - P;
     double* Ln = Lring + jslot(s0, 0, jring, st);
     const double chi = f[3 * M + m];
@@ -678,7 +688,7 @@ __global__ void k_adj_vacuum(long long M, int U, int V, int W, const double* __r
 
 __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __restrict__ Ln,
                            const double* __restrict__ lam_vac, const double* __restrict__ J,
-                           int j_first, int n, int n_taps, double* __restrict__ grad_chi,
+                           int j_first, int n, Taps tp, double* __restrict__ grad_chi,
                            double* __restrict__ lam_out) {
     const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
@@ -689,9 +699,9 @@ __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __
         if (ichi > 0.0) {
             lam = Ln[beta * M + m] * ichi;
             double q = 0.0;
-            const int L = n_taps > 2 ? n_taps : 2;
+            const int L = tp.n > 2 ? tp.n : 2;
             for (int l = 0; l < L && n - l >= 1; ++l) {   // J[0] holds step j_first
-                const double w = (l < 2 ? 0.5 : 0.0) + (l < n_taps ? c_taps[l] : 0.0);
+                const double w = (l < 2 ? 0.5 : 0.0) + (l < tp.n ? tp.d[l] : 0.0);
                 q += w * J[((long long)(n - l - j_first) * M + m) * 3 + beta];
             }
             gsum += lam * q * ichi;
@@ -708,7 +718,7 @@ __global__ void k_adj_post(long long M, const double* __restrict__ f, double* __
 template <typename R>
 __global__ void k_history_out(long long M, const double* __restrict__ eps,
                               const double* __restrict__ chi, const R* __restrict__ hist,
-                              const double* __restrict__ Jring, int s0, int jring, int n_taps,
+                              const double* __restrict__ Jring, int s0, int jring, Taps tp,
                               double* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * M) return;
@@ -716,12 +726,13 @@ __global__ void k_history_out(long long M, const double* __restrict__ eps,
     const int beta = (int)(i / M);
     const long long st = 3 * M;
     double P = 0.5 / eps[m] * Jring[jslot(s0, 1, jring, st) + i] - chi[m] * (double)hist[i];
-    for (int l = 1; l < n_taps; ++l) P += c_taps[l] * Jring[jslot(s0, l, jring, st) + i];
+    for (int l = 1; l < tp.n; ++l) P += tp.d[l] * Jring[jslot(s0, l, jring, st) + i];
     out[m * 3 + beta] = P;
 }
 
 // y = A x (FP64) on active voxels, for the setup-time eigenvalue estimate
-__global__ void k_apply64(CGArgs a, const double* __restrict__ x, double* __restrict__ y) {
+__global__ void k_apply64(const __grid_constant__ CGArgs a, const double* __restrict__ x,
+                          double* __restrict__ y) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.nact) return;
     const int m = a.act[i];
@@ -789,25 +800,34 @@ void stencil_setup(mot_ctx* c) {
                 c->stencil[k + 4] = (ex && ez) ? src[4] * sx * sz : 0.0;
                 c->stencil[k + 5] = (ey && ez) ? src[5] * sy * sz : 0.0;
             }
-    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stencil, c->stencil, sizeof(double) * 27 * 6));
-    float st32[27 * 6];
-    float stl[27 * 6];
-    for (int k = 0; k < 27 * 6; ++k) {
-        st32[k] = (float)c->stencil[k];
-        stl[k] = (float)(c->stencil[k] - (double)st32[k]);
+    // The stencil constants are shared by every context on the device: G_0 at offsets
+    // |d_i| <= 1 depends on the unit voxel only, so all contexts compute the same
+    // values.  A grid of extent 1 along some axis lacks those neighbours (its entries
+    // are zero, and masked out of its own stencil), so it writes the constants only
+    // while no complete stencil is there.
+    const bool complete = c->U > 1 && c->V > 1 && c->W > 1;
+    int dev = 0;
+    MOT_CUDA_TRY(cudaGetDevice(&dev));
+    static bool have_complete[64] = {};
+    if (complete || dev >= 64 || !have_complete[dev]) {
+        MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stencil, c->stencil, sizeof(double) * 27 * 6));
+        float st32[27 * 6];
+        float stl[27 * 6];
+        for (int k = 0; k < 27 * 6; ++k) {
+            st32[k] = (float)c->stencil[k];
+            stl[k] = (float)(c->stencil[k] - (double)st32[k]);
+        }
+        MOT_CUDA_TRY(cudaMemcpyToSymbol(c_st32, st32, sizeof st32));
+        MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stl, stl, sizeof stl));
+        if (complete && dev < 64) have_complete[dev] = true;
     }
-    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_st32, st32, sizeof st32));
-    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_stl, stl, sizeof stl));
     int noff[27];
     for (int ez = -1; ez <= 1; ++ez)
         for (int ey = -1; ey <= 1; ++ey)
             for (int ex = -1; ex <= 1; ++ex)
                 noff[(ez + 1) * 9 + (ey + 1) * 3 + (ex + 1)] = ex + c->U * (ey + c->V * ez);
-    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_noff, noff, sizeof noff));
-    double taps[MAXTAPS] = {0};
+    for (int e = 0; e < 27; ++e) c->noff[e] = noff[e];
     if (c->n_taps > MAXTAPS) throw MotError{MOT_ERR_ARG, "at most 64 FIR taps are supported"};
-    for (int i = 0; i < c->n_taps; ++i) taps[i] = c->taps[i];
-    MOT_CUDA_TRY(cudaMemcpyToSymbol(c_taps, taps, sizeof(double) * MAXTAPS));
     int per_sm = 0;
     if (c->precision == MOT_FP64)
         MOT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<false>, NT, 0));
@@ -876,6 +896,7 @@ void chebyshev_setup(mot_ctx* c) {
         MOT_CUDA_TRY(cudaMemset(v0, 0, sizeof(double) * n3));
         CGArgs a{};
         a.M = c->M; a.act = c->active; a.nmask = c->nmask; a.nact = c->nact; a.diag = c->cg_diag;
+        for (int e = 0; e < 27; ++e) a.noff[e] = c->noff[e];
         auto dot = [&](const double* x, const double* y) {
             k_dot<<<nb, NT, 0, c->stream>>>(x, y, n3, part);
             MOT_LAUNCH_CHECK();
@@ -947,13 +968,14 @@ void epilogue(mot_ctx* c, int n, const double* En, cudaStream_t s) {
     const long long tot = 3 * c->M;
     k_epilogue<R><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
         c->M, c->vfac, En, hbuf<R>(c).hist_spatial, c->J, (int)slot_index(n, c->jring), c->jring,
-        c->n_taps, c->rhs);
+        taps_of(c), c->rhs);
     MOT_LAUNCH_CHECK();
 }
 
 CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
     CGArgs a;
     a.M = c->M;
+    for (int e = 0; e < 27; ++e) a.noff[e] = c->noff[e];
     a.act = c->active;
     a.nmask = c->nmask;
     a.nact = c->nact;
@@ -1021,11 +1043,11 @@ void history_out(mot_ctx* c, int n, double* out_dev, cudaStream_t s) {
     if (c->precision == MOT_FP64)
         k_history_out<double><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
             c->M, c->eps, c->chi, c->h64.hist_spatial, c->J, (int)slot_index(n, c->jring), c->jring,
-            c->n_taps, out_dev);
+            taps_of(c), out_dev);
     else
         k_history_out<float><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
             c->M, c->eps, c->chi, c->h32.hist_spatial, c->J, (int)slot_index(n, c->jring), c->jring,
-            c->n_taps, out_dev);
+            taps_of(c), out_dev);
     MOT_LAUNCH_CHECK();
 }
 
@@ -1037,10 +1059,10 @@ void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double*
     const int s0 = (int)slot_index(tau, c->jring);
     if (c->precision == MOT_FP64)
         k_epilogue_adj<double><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
-            c->M, c->vfac, g_aos, c->h64.hist_spatial, c->J, s0, c->jring, c->n_taps, c->rhs);
+            c->M, c->vfac, g_aos, c->h64.hist_spatial, c->J, s0, c->jring, taps_of(c), c->rhs);
     else
         k_epilogue_adj<float><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
-            c->M, c->vfac, g_aos, c->h32.hist_spatial, c->J, s0, c->jring, c->n_taps, c->rhs);
+            c->M, c->vfac, g_aos, c->h32.hist_spatial, c->J, s0, c->jring, taps_of(c), c->rhs);
     MOT_LAUNCH_CHECK();
     CGArgs a = make_cg_args(c, tau, norm2_out);
     void* args[] = {&a};
@@ -1050,7 +1072,7 @@ void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double*
                                                            c->rhs, c->cg_q);
     MOT_LAUNCH_CHECK();
     k_adj_post<<<(int)((c->M + NT - 1) / NT), NT, 0, s>>>(c->M, c->vfac, mu, c->cg_q, J_aos,
-                                                         j_first, n, c->n_taps, grad_chi,
+                                                         j_first, n, taps_of(c), grad_chi,
                                                          lam_out);
     MOT_LAUNCH_CHECK();
     c->stats.launches += 4;

@@ -11,6 +11,7 @@ m = u + U (v + V w) and b = x, y, z.
 """
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -25,7 +26,8 @@ STATUS_NAMES = {0: "MOT_OK", 1: "MOT_ERR_ARG", 2: "MOT_ERR_OOM", 3: "MOT_ERR_CUD
 PRECISIONS = {"fp64": 0, "fp32_history": 1}
 SCHEMES = {"direct": 0, "blocked": 1}
 
-EXPORTS = ["mot_create", "mot_destroy", "mot_set_excitation", "mot_plane_wave",
+EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation",
+           "mot_plane_wave",
            "mot_plane_wave_static", "mot_march", "mot_restart", "mot_adjoint_begin",
            "mot_adjoint_run", "mot_adjoint_end",
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
@@ -74,6 +76,7 @@ def load_library(path=LIB_PATH):
     lib.mot_adjoint_run.argtypes = [P, I, P, I, I, P, P, P]
     lib.mot_adjoint_end.argtypes = [P, P, P]
     lib.mot_restart.argtypes = [P, I, I, P, P]
+    lib.mot_create_shared.argtypes = [P, ctypes.POINTER(P)]
     lib.mot_get_table.argtypes = [P, I, I, P]
     lib.mot_get_spectrum.argtypes = [P, I, P]
     lib.mot_get_info.argtypes = [P, P, P, P, P, P, P]
@@ -156,8 +159,28 @@ class Context:
         if st != MOT_OK:
             raise MotError(st, self._lib.mot_last_error(self._h).decode())
 
+    def share(self):
+        """A second, independent marching state on this context's setup
+        (mot_create_shared); this context is kept alive as long as the new one."""
+        out = ctypes.c_void_p()
+        st = self._lib.mot_create_shared(self._h, ctypes.byref(out))
+        if st != MOT_OK:
+            raise MotError(st, self._lib.mot_last_error(None).decode())
+        c = Context.__new__(Context)
+        c.shape, c.M, c._lib = self.shape, self.M, self._lib
+        c._scheme, c._precision, c._block = self._scheme, self._precision, self._block
+        c.ell, c.P = self.ell, self.P
+        c._h = out
+        c._src = self
+        self._shares = [r for r in getattr(self, "_shares", []) if r() is not None]
+        self._shares.append(weakref.ref(c))
+        return c
+
     def close(self):
         if getattr(self, "_h", None):
+            live = [r() for r in getattr(self, "_shares", [])]
+            if any(c is not None and getattr(c, "_h", None) for c in live):
+                raise RuntimeError("close the contexts shared from this one first")
             self._lib.mot_destroy(self._h)
             self._h = None
 
