@@ -343,10 +343,43 @@ def oracle_sample(steps, warmup):
                       "%d steps (element table and LU setup untimed)" % (N, steps)}
 
 
+def run_batched_bench(args, world):
+    """Config of uneven scatterers x excitations (workloads.batched_instances): the
+    marches of every scatterer and excitation, FP32-history, blocked scheme with B
+    tuned per size bucket; a bench step = 128 time steps of every march.  Setup and
+    tuning (which also warms every kernel variant up) are outside the timed region."""
+    import torch
+    from paper_2407_03323_gb300.batch import BlockTuner, run_batched
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    inst = wl.batched_instances()
+    tuner = BlockTuner("fp32_history")
+    n_steps = 128 * args.steps
+    res = run_batched(inst, n_steps, tuner=tuner)
+    value = world * res["value"]
+    return {"metric": "voxel-timesteps/s", "value": value, "unit": "voxel-timesteps/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * res["march_s"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 history + double-float CG residual + f64 state", "data": "synthetic",
+            "config": {"workload": "%d scatterers (sides %d..%d, sphere/cube, eps_r 2..30) x %d "
+                                   "plane waves, FIR3, %d time steps"
+                                   % (len(inst), min(x["N"] for x in inst),
+                                      max(x["N"] for x in inst), len(inst[0]["waves"]), n_steps),
+                       "blocks": res["blocks"], "memory_waves": res["waves"],
+                       "setup_s": res["setup_s"], "tuning_s_per_step": res["tuning"],
+                       "warmup": "block-size tuning marches of every bucket",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"}}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl != "reference" and args.config.startswith("batched"):
+        line = run_batched_bench(args, world)
+        if rank == 0:
+            print(json.dumps(line))
+        return
     if args.impl == "reference":
         if rank != 0:
             return

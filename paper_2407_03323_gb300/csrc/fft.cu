@@ -232,10 +232,18 @@ template <typename R> size_t smem_bytes(int P) {
     return sizeof(C) * ((size_t)P + 2 * (size_t)P * (Tile<R>::TB + 1));
 }
 
-// dynamic shared memory of a pass kernel; prefer the largest shared-memory carveout so
-// that several of its tiles are resident per SM
+// Dynamic shared memory of a pass kernel.  The limit is a process-wide attribute of
+// the kernel, and contexts of different sizes may launch it from several threads, so
+// it is set to the device's opt-in maximum (a value that never changes) rather than
+// to one launch's need; the need is checked against it.  The largest shared-memory
+// carveout is preferred so that several tiles are resident per SM.
 template <typename K> void set_smem(K kern, size_t bytes) {
-    MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    int dev = 0, optin = 0;
+    MOT_CUDA_TRY(cudaGetDevice(&dev));
+    MOT_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (bytes > (size_t)optin)
+        throw MotError{MOT_ERR_ARG, "FFT length too large for one shared-memory tile"};
+    MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
 }
 

@@ -867,7 +867,14 @@ void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     const size_t sm = sizeof(C) * ((size_t)P + 2 * (size_t)P * (3 * TB + 1));
     if (sm > 220 * 1024 || a.S > kMaxLevel)
         throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
-    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // the limit is process-wide and P varies by level and context: set the device's
+    // opt-in maximum (never lowered by another launch), the need is checked above
+    int dev = 0, optin = 0;
+    MOT_CUDA_TRY(cudaGetDevice(&dev));
+    MOT_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (sm > (size_t)optin)
+        throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     MOT_CUDA_TRY(cudaFuncSetAttribute(k_far<R, TB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     const long long blocks = (long long)c->Hw * c->Hv * 4 * a.ntile;
     k_far<R, TB><<<(int)blocks, NT, sm, s>>>(a);

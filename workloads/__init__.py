@@ -90,6 +90,25 @@ def random_directions(n, seed):
     return out
 
 
+def batched_instances(n_instances=24, n_rhs=8, seed=MASTER_SEED, side_range=(16, 48)):
+    """Uneven batch of scatterers: sides uniform on side_range, a sphere or a cube
+    with probability 1/2, eps_r uniform on [2, 30], n_rhs plane waves per scatterer
+    (directions uniform on S^2, random orthogonal polarisation), FIR3 with
+    delta = 1e-7 M.  All draws from numpy.random.default_rng(seed) in that order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_instances):
+        N = int(rng.integers(side_range[0], side_range[1] + 1))
+        is_sphere = bool(rng.integers(0, 2))
+        eps = float(rng.uniform(2.0, 30.0))
+        geom = sphere(N, eps) if is_sphere else cube(N, eps)
+        waves = [pulse(N, eps, k_hat=k, p_hat=pp)
+                 for k, pp in random_directions(n_rhs, int(rng.integers(0, 2 ** 31)))]
+        out.append({"N": N, "shape": "sphere" if is_sphere else "cube", "eps": eps,
+                    "eps_r": geom, "taps": fir_taps("fir3", 1e-7 * N ** 3), "waves": waves})
+    return out
+
+
 # ---------------------------------------------------------------- FIR taps
 
 def fir_taps(kind, delta=0.0):
