@@ -215,6 +215,70 @@ __global__ void __launch_bounds__(NT) k_mid(const typename CT<R>::c* __restrict_
     }
 }
 
+// ------------------------------------------------------------------ strided passes, four-step
+// Length P = P1 P2 with both factors small: n = n1 + P1 n2, k = k2 + P2 k1,
+//   X[k2 + P2 k1] = sum_{n1} W_P1^{n1 k1} (W_P^{n1 k2} sum_{n2} x[n1 + P1 n2] W_P2^{n2 k2}).
+// A CTA holds 32 consecutive lines (lane = line, so every load and store is one
+// coalesced run); phase A: warp n1 loads its P2 strided inputs (only the unpadded
+// ones), runs the P2-point DFT in registers (compile-time structure and roots) and
+// applies W_P^{n1 k2}; phase B: warp k2 gathers the P1 values over n1 from shared
+// memory, runs the P1-point DFT and stores the outputs the pass needs.
+template <typename R, int P1, int P2, int DIR>
+__global__ void __launch_bounds__(32 * (P1 > P2 ? P1 : P2))
+k_mid4s(const typename CT<R>::c* __restrict__ in, typename CT<R>::c* __restrict__ out,
+        const typename CT<R>::c* __restrict__ tw, MidArgs a) {
+    typedef typename CT<R>::c C;
+    constexpr int P = P1 * P2, NL = 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* Y = reinterpret_cast<C*>(smem_raw);          // [P1][P2][NL]
+    C* stw = Y + P * NL;                            // [P] roots exp(-2 pi i k / P)
+    const int ntile = (a.Hu + NL - 1) / NL;
+    const long long o = blockIdx.x / ntile;
+    const int ku0 = (int)(blockIdx.x % ntile) * NL;
+    const long long comp = o / a.n_o2, o2 = o % a.n_o2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool live = ku0 + lane < a.Hu;
+    const C* src = in + comp * a.in_c + o2 * a.in_o + ku0 + lane;
+    C* dst = out + comp * a.out_c + o2 * a.out_o + ku0 + lane;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    __syncthreads();
+    if (warp < P1) {
+        const int n1 = warp;
+        C x[P2];
+        Unroll1<0, P2>::run([&](auto q) {
+            constexpr int n2 = decltype(q)::value;
+            const int idx = n1 + P1 * n2;
+            C v;
+            v.x = 0; v.y = 0;
+            if (idx < a.n_in && live) v = src[(long long)idx * a.in_a];
+            x[n2] = v;
+        });
+        dft_ct<P2, DIR>(x);
+        Unroll1<0, P2>::run([&](auto q) {
+            constexpr int k2 = decltype(q)::value;
+            C w = stw[(n1 * k2) % P];
+            if (DIR > 0) w.y = -w.y;
+            Y[(n1 * P2 + k2) * NL + lane] = cmul(x[k2], w);
+        });
+    }
+    __syncthreads();
+    if (warp < P2) {
+        const int k2 = warp;
+        C y[P1];
+        Unroll1<0, P1>::run([&](auto q) {
+            constexpr int n1 = decltype(q)::value;
+            y[n1] = Y[(n1 * P2 + k2) * NL + lane];
+        });
+        dft_ct<P1, DIR>(y);
+        if (!live) return;
+        Unroll1<0, P1>::run([&](auto q) {
+            constexpr int k1 = decltype(q)::value;
+            const int k = k2 + P2 * k1;
+            if (k < a.n_out) dst[(long long)k * a.out_a] = y[k1];
+        });
+    }
+}
+
 RadixList radix_list(const AxisFFT& ax) {
     RadixList rl;
     rl.P = ax.P;
@@ -245,6 +309,44 @@ template <typename K> void set_smem(K kern, size_t bytes) {
         throw MotError{MOT_ERR_ARG, "FFT length too large for one shared-memory tile"};
     MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     MOT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+}
+
+template <typename R, int P1, int P2>
+void launch_mid4s(const typename CT<R>::c* in, typename CT<R>::c* out,
+                  const typename CT<R>::c* tw, const MidArgs& a, int nblocks, cudaStream_t s) {
+    typedef typename CT<R>::c C;
+    const size_t sm = sizeof(C) * ((size_t)P1 * P2 * 32 + (size_t)P1 * P2);
+    constexpr int threads = 32 * (P1 > P2 ? P1 : P2);
+    if (a.dir < 0) {
+        set_smem(k_mid4s<R, P1, P2, -1>, sm);
+        k_mid4s<R, P1, P2, -1><<<nblocks, threads, sm, s>>>(in, out, tw, a);
+    } else {
+        set_smem(k_mid4s<R, P1, P2, +1>, sm);
+        k_mid4s<R, P1, P2, +1><<<nblocks, threads, sm, s>>>(in, out, tw, a);
+    }
+    MOT_LAUNCH_CHECK();
+}
+
+// a strided pass of length ax.P over [3][n_o2] x Hu lines: the four-step kernel for the
+// lengths that have a factor pair below, the generic Stockham tile otherwise
+template <typename R>
+void mid_pass(const typename CT<R>::c* in, typename CT<R>::c* out, const AxisFFT& ax,
+              const MidArgs& a, cudaStream_t s) {
+    const int P = ax.P;
+    const long long lines = 3LL * a.n_o2;
+    const int nb32 = (int)(lines * ((a.Hu + 31) / 32));
+    switch (P) {
+        case 64: launch_mid4s<R, 8, 8>(in, out, table<R>(ax), a, nb32, s); return;
+        case 96: launch_mid4s<R, 8, 12>(in, out, table<R>(ax), a, nb32, s); return;
+        case 210: launch_mid4s<R, 14, 15>(in, out, table<R>(ax), a, nb32, s); return;
+        default: break;
+    }
+    constexpr int TB = Tile<R>::TB;
+    const size_t sm = smem_bytes<R>(P);
+    set_smem(k_mid<R>, sm);
+    k_mid<R><<<(int)(lines * ((a.Hu + TB - 1) / TB)), NT, sm, s>>>(in, out, table<R>(ax),
+                                                                    radix_list(ax), a);
+    MOT_LAUNCH_CHECK();
 }
 
 __global__ void twiddle_kernel(int P, double2* t64, float2* t32) {
@@ -301,7 +403,6 @@ void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStr
                                                                  radix_list(c->ax[0]), scale);
         MOT_LAUNCH_CHECK();
     }
-    const int ntile = (Hu + TB - 1) / TB;
     // y: [3][W][V][Hu] -> [3][W][Pv][Hu]
     {
         MidArgs a;
@@ -309,11 +410,7 @@ void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStr
         a.in_c = (long long)W * V * Hu; a.in_o = (long long)V * Hu; a.in_a = Hu;
         a.out_c = (long long)W * Pv * Hu; a.out_o = (long long)Pv * Hu; a.out_a = Hu;
         a.Hu = Hu; a.dir = -1;
-        const size_t sm = smem_bytes<R>(Pv);
-        set_smem(k_mid<R>, std::max(sm, smem_bytes<R>(Pw)));
-        k_mid<R><<<3 * W * ntile, NT, sm, s>>>(hb.tmp1, hb.tmp2, table<R>(c->ax[1]),
-                                               radix_list(c->ax[1]), a);
-        MOT_LAUNCH_CHECK();
+        mid_pass<R>(hb.tmp1, hb.tmp2, c->ax[1], a, s);
     }
     // z: [3][W][Pv][Hu] -> [3][Pw][Pv][Hu]
     {
@@ -322,10 +419,7 @@ void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStr
         a.in_c = (long long)W * Pv * Hu; a.in_o = Hu; a.in_a = (long long)Pv * Hu;
         a.out_c = (long long)Pw * Pv * Hu; a.out_o = Hu; a.out_a = (long long)Pv * Hu;
         a.Hu = Hu; a.dir = -1;
-        const size_t sm = smem_bytes<R>(Pw);
-        k_mid<R><<<3 * Pv * ntile, NT, sm, s>>>(hb.tmp2, out, table<R>(c->ax[2]),
-                                                radix_list(c->ax[2]), a);
-        MOT_LAUNCH_CHECK();
+        mid_pass<R>(hb.tmp2, out, c->ax[2], a, s);
     }
 }
 
@@ -335,7 +429,6 @@ void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s
     constexpr int TB = Tile<R>::TB;
     const int U = c->U, V = c->V, W = c->W;
     const int Pu = c->ax[0].P, Pv = c->ax[1].P, Pw = c->ax[2].P, Hu = c->Hu;
-    const int ntile = (Hu + TB - 1) / TB;
     // z: [3][Pw][Pv][Hu] -> [3][W][Pv][Hu]
     {
         MidArgs a;
@@ -343,11 +436,7 @@ void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s
         a.in_c = (long long)Pw * Pv * Hu; a.in_o = Hu; a.in_a = (long long)Pv * Hu;
         a.out_c = (long long)W * Pv * Hu; a.out_o = Hu; a.out_a = (long long)Pv * Hu;
         a.Hu = Hu; a.dir = +1;
-        const size_t sm = smem_bytes<R>(Pw);
-        set_smem(k_mid<R>, std::max(sm, smem_bytes<R>(Pv)));
-        k_mid<R><<<3 * Pv * ntile, NT, sm, s>>>(in, hb.tmp2, table<R>(c->ax[2]),
-                                                radix_list(c->ax[2]), a);
-        MOT_LAUNCH_CHECK();
+        mid_pass<R>(in, hb.tmp2, c->ax[2], a, s);
     }
     // y: [3][W][Pv][Hu] -> [3][W][V][Hu]
     {
@@ -356,10 +445,7 @@ void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s
         a.in_c = (long long)W * Pv * Hu; a.in_o = (long long)Pv * Hu; a.in_a = Hu;
         a.out_c = (long long)W * V * Hu; a.out_o = (long long)V * Hu; a.out_a = Hu;
         a.Hu = Hu; a.dir = +1;
-        const size_t sm = smem_bytes<R>(Pv);
-        k_mid<R><<<3 * W * ntile, NT, sm, s>>>(hb.tmp2, hb.tmp1, table<R>(c->ax[1]),
-                                               radix_list(c->ax[1]), a);
-        MOT_LAUNCH_CHECK();
+        mid_pass<R>(hb.tmp2, hb.tmp1, c->ax[1], a, s);
     }
     // x: c2r
     {

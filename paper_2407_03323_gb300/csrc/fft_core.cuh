@@ -12,13 +12,13 @@ namespace mot_fft {
 
 // compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1
 template <int B, int E> struct Unroll1 {
-    template <typename F> __device__ __forceinline__ static void run(F&& f) {
+    template <typename F> __host__ __device__ __forceinline__ static void run(F&& f) {
         f(std::integral_constant<int, B>());
         Unroll1<B + 1, E>::run(f);
     }
 };
 template <int E> struct Unroll1<E, E> {
-    template <typename F> __device__ __forceinline__ static void run(F&&) {}
+    template <typename F> __host__ __device__ __forceinline__ static void run(F&&) {}
 };
 
 // Twiddles known at compile time: cos and sin of 2 pi k / n by the Taylor series of
@@ -62,6 +62,109 @@ static_assert(root_of_unity(1, 6).re - 0.5 < 1e-16 && 0.5 - root_of_unity(1, 6).
               "twiddle");
 static_assert(root_of_unity(1, 8).re - 0.70710678118654752 < 2e-16 &&
               0.70710678118654752 - root_of_unity(1, 8).re < 2e-16, "twiddle");
+
+// v * W_N^K for compile-time K, N; DIR = -1 forward (W = exp(-2 pi i / N)), +1 inverse
+template <int K, int N, int DIR, typename C>
+__host__ __device__ __forceinline__ C twiddle_c(C v) {
+    typedef decltype(v.x) R;
+    if constexpr (K == 0) {
+        return v;
+    } else if constexpr (4 * K == N) {        // -i (forward) / +i (inverse)
+        C o;
+        if (DIR < 0) { o.x = v.y; o.y = -v.x; } else { o.x = -v.y; o.y = v.x; }
+        return o;
+    } else {
+        constexpr CTw w = root_of_unity(K, N);
+        constexpr R wr = (R)w.re;
+        constexpr R wi = (R)(DIR < 0 ? w.im : -w.im);
+        C o;
+        o.x = v.x * wr - v.y * wi;
+        o.y = v.x * wi + v.y * wr;
+        return o;
+    }
+}
+
+// In-register DFT of N = 2^a 3^b 5^c 7^d points with compile-time structure:
+// X[k] = sum_n x[n] W_N^{nk}, W_N = exp(-2 pi i / N) (DIR = -1) or its conjugate
+// (DIR = +1); natural order in and out.  Composite N by decimation in time with the
+// smallest factor R first: with n = r + R m and k = k1 + M q (M = N / R),
+//   X[k1 + M q] = sum_r W_R^{r q} (W_N^{r k1} sum_m x[r + R m] W_M^{m k1}).
+// Odd primes use the symmetric form out[q] = x0 + sum_r (s_r cos - / + i d_r sin)
+// with s_r = x_r + x_{R-r}, d_r = x_r - x_{R-r}.
+constexpr int smallest_factor(int n) {
+    return n % 2 == 0 ? 2 : (n % 3 == 0 ? 3 : (n % 5 == 0 ? 5 : 7));
+}
+
+template <int N, int DIR, typename C>
+__host__ __device__ __forceinline__ void dft_ct(C* x) {
+    typedef decltype(x[0].x) Rl;
+    if constexpr (N == 1) {
+        return;
+    } else if constexpr (N == 2) {
+        const C a = x[0], b = x[1];
+        x[0] = cadd(a, b);
+        x[1] = csub(a, b);
+    } else if constexpr (N == 3 || N == 5 || N == 7) {
+        constexpr int H = (N - 1) / 2;
+        C s[H], d[H];
+        const C v0 = x[0];
+        C sum = v0;
+        Unroll1<1, H + 1>::run([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            s[r - 1] = cadd(x[r], x[N - r]);
+            d[r - 1] = csub(x[r], x[N - r]);
+            sum = cadd(sum, s[r - 1]);
+        });
+        Unroll1<1, H + 1>::run([&](auto qc) {
+            constexpr int q = decltype(qc)::value;
+            C A = v0, B;
+            B.x = 0; B.y = 0;
+            Unroll1<1, H + 1>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                constexpr CTw w = root_of_unity((q * r) % N, N);   // cos - i sin
+                constexpr Rl cs = (Rl)w.re, sn = (Rl)(-w.im);
+                A.x += s[r - 1].x * cs;
+                A.y += s[r - 1].y * cs;
+                B.x += d[r - 1].x * sn;
+                B.y += d[r - 1].y * sn;
+            });
+            C mB;   // -i B
+            mB.x = B.y; mB.y = -B.x;
+            if constexpr (DIR < 0) {
+                x[q] = cadd(A, mB);
+                x[N - q] = csub(A, mB);
+            } else {
+                x[q] = csub(A, mB);
+                x[N - q] = cadd(A, mB);
+            }
+        });
+        x[0] = sum;
+    } else {
+        constexpr int R = smallest_factor(N), M = N / R;
+        C sub[R][M];
+        Unroll1<0, R>::run([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            Unroll1<0, M>::run([&](auto mc) {
+                constexpr int m = decltype(mc)::value;
+                sub[r][m] = x[r + R * m];
+            });
+            dft_ct<M, DIR>(sub[r]);
+        });
+        Unroll1<0, M>::run([&](auto kc) {
+            constexpr int k1 = decltype(kc)::value;
+            C v[R];
+            Unroll1<0, R>::run([&](auto rc) {
+                constexpr int r = decltype(rc)::value;
+                v[r] = twiddle_c<(r * k1) % N, N, DIR>(sub[r][k1]);
+            });
+            dft_ct<R, DIR>(v);
+            Unroll1<0, R>::run([&](auto qc) {
+                constexpr int q = decltype(qc)::value;
+                x[k1 + M * q] = v[q];
+            });
+        });
+    }
+}
 
 // dir = -1 forward (exp(-i...)), +1 inverse; W(m) = exp(dir 2 pi i m / P) from table
 template <typename C>

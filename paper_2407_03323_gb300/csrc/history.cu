@@ -414,27 +414,6 @@ template <int E> struct Unroll<E, E> {
     template <typename F> __device__ __forceinline__ static void run(F&&) {}
 };
 
-// v * W_N^K for compile-time K, N; DIR = -1 forward (W = exp(-2 pi i / N)), +1 inverse
-template <int K, int N, int DIR, typename C>
-__device__ __forceinline__ C twiddle_c(C v) {
-    typedef decltype(v.x) R;
-    if constexpr (K == 0) {
-        return v;
-    } else if constexpr (4 * K == N) {        // -i (forward) / +i (inverse)
-        C o;
-        if (DIR < 0) { o.x = v.y; o.y = -v.x; } else { o.x = -v.y; o.y = v.x; }
-        return o;
-    } else {
-        constexpr CTw w = root_of_unity(K, N);
-        constexpr R wr = (R)w.re;
-        constexpr R wi = (R)(DIR < 0 ? w.im : -w.im);
-        C o;
-        o.x = v.x * wr - v.y * wi;
-        o.y = v.x * wi + v.y * wr;
-        return o;
-    }
-}
-
 // Lines of length P = T * Q are split over T threads; thread t holds positions
 // t Q .. t Q + Q - 1 of the (natural- or bit-reversed-order) line.  Stages whose span
 // reaches across threads exchange values with the partner thread by warp shuffles

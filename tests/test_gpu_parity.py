@@ -307,3 +307,36 @@ def test_long_grid_levels_to_128(mot):
     assert np.linalg.norm(ref[-1]) > 1e-3 * np.abs(ref).max()
     assert rel_l2(out[("blocked", "fp64")], ref) < 1e-12
     assert rel_l2(out[("blocked", "fp32_history")], ref) < 1e-5
+
+
+def test_long_axis_through_every_pass_kernel(mot):
+    """One heterogeneous problem with a 104-voxel axis (padded length 210) marched with
+    that axis along z, y and x: the strided passes (z, y) and the real-to-complex pass
+    (x) are different kernels, so the three marches agree only if each is right
+    (components and axes permuted back; FP64, direct scheme)."""
+    rng = np.random.default_rng(12)
+    base = 2.0 + 8.0 * rng.uniform(size=(104, 4, 5))        # [w][v][u], long axis w
+    taps = wl.fir_taps("fir3", 1e-3)
+    p = wl.pulse(0, 6.0, k_hat=(0.3, 0.5, 0.81), p_hat=(0.2, -0.9, 0.3))
+    k = np.asarray(p["k_hat"]); pp = np.asarray(p["p_hat"])
+    steps = 60
+    # axis permutations of (x, y, z) = (u, v, w): the grid axes [w][v][u] move with them
+    cases = {"z": ((0, 1, 2), base),                          # identity
+             "y": ((0, 2, 1), base.transpose(1, 0, 2)),       # swap y <-> z: [v][w][u] -> long v
+             "x": ((2, 1, 0), base.transpose(2, 1, 0))}       # swap x <-> z: long u
+    out = {}
+    for name, (perm, eps) in cases.items():
+        kk, pq = k[list(perm)], pp[list(perm)]
+        with mot.Context(eps, taps) as ctx:
+            assert 210 in ctx.P
+            E = ctx.plane_wave(kk, pq, p["f_c"], p["sigma_t"], p["t0"] - 60, 1, steps)
+            ctx.set_excitation(E)
+            J = ctx.march(steps).reshape(steps, *eps.shape, 3)
+        out[name] = J
+    ref = out["z"]
+    y = out["y"].transpose(0, 2, 1, 3, 4)[..., [0, 2, 1]]     # back to [w][v][u], comps x z y
+    x = out["x"].transpose(0, 3, 2, 1, 4)[..., [2, 1, 0]]
+    nrm = np.linalg.norm(ref)
+    assert nrm > 0
+    assert np.linalg.norm(y - ref) < 1e-12 * nrm
+    assert np.linalg.norm(x - ref) < 1e-12 * nrm
