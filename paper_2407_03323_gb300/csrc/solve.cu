@@ -260,11 +260,13 @@ __device__ __forceinline__ void stencil_pairs_df(V&& load, int mask, float* oh, 
     stencil_pair_df<26, FULL>(load, mask, oh, ol);
 }
 
-// r = b - A x at an active voxel in double-float, rounded to FP32
-__device__ __forceinline__ float4 residual_df(const CGArgs& a, int m, int mask) {
+// r = b - A x at an active voxel in double-float, rounded to FP32.  ch, cl: the voxel's
+// x pair; dh, dl: its diagonal; bh, bl: its b pair; load(e, sh, sl) adds the x pair of
+// neighbour e (compile-time index) to (sh, sl).
+template <bool FULL, typename V>
+__device__ __forceinline__ float4 residual_df_at(float4 ch, float4 cl, float dh, float dl,
+                                                 float4 bh, float4 bl, V&& load, int mask) {
     float oh[3] = {0.f, 0.f, 0.f}, ol[3] = {0.f, 0.f, 0.f};   // o = A x
-    const float4 ch = a.xh[m], cl = a.xl[m];
-    const float dh = a.diag32[m], dl = a.diag_lo[m];
     const float* H0 = c_st32 + 13 * 6;
     const float* L0 = c_stl + 13 * 6;
     // centre block: (d - G_0(0)) x; G_0(0) is diagonal (parity)
@@ -274,17 +276,8 @@ __device__ __forceinline__ float4 residual_df(const CGArgs& a, int m, int mask) 
     df_msub(H0[0], L0[0], ch.x, cl.x, oh[0], ol[0]);
     df_msub(H0[1], L0[1], ch.y, cl.y, oh[1], ol[1]);
     df_msub(H0[2], L0[2], ch.z, cl.z, oh[2], ol[2]);
-    auto load = [&](auto e, float* sh, float* sl) {
-        const int m2 = m + a.noff[decltype(e)::value];
-        const float4 vh = a.xh[m2], vl = a.xl[m2];
-        df_add(sh[0], sl[0], vh.x, vl.x);
-        df_add(sh[1], sl[1], vh.y, vl.y);
-        df_add(sh[2], sl[2], vh.z, vl.z);
-    };
     // o = (d - G_0(0)) x - sum_pairs G_0(e) (x_e + x_-e) = A x
-    if (mask == kAllNeighbours) stencil_pairs_df<true>(load, mask, oh, ol);
-    else stencil_pairs_df<false>(load, mask, oh, ol);
-    const float4 bh = a.bh[m], bl = a.bl[m];
+    stencil_pairs_df<FULL>(load, mask, oh, ol);
     float r[3];
     const float bhv[3] = {bh.x, bh.y, bh.z}, blv[3] = {bl.x, bl.y, bl.z};
 #pragma unroll
@@ -314,6 +307,9 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait1() {   // all but the newest group landed
     asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_wait0() {   // every group landed
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 // halo (TH^3, zero outside the grid) of d around the tile with origin `org`
 __device__ __forceinline__ void load_halo(const CGArgs& a, const float4* __restrict__ dk,
@@ -335,8 +331,8 @@ __device__ __forceinline__ void load_halo(const CGArgs& a, const float4* __restr
 constexpr int kVoxPerThread = TT * TT * TT / NT;
 static_assert(kVoxPerThread * NT == TT * TT * TT, "tile voxels per thread");
 __device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* __restrict__ dk,
-                                                float4* __restrict__ dn, float c1, float c2) {
-    __shared__ float4 sd[2][TH * TH * TH];
+                                                float4* __restrict__ dn, float c1, float c2,
+                                                float4 (*sd)[TH * TH * TH]) {
     const long long UV = (long long)a.U * a.V;
     int tile = blockIdx.x;
     if (tile < a.ntiles) load_halo(a, dk, sd[0], a.tiles[tile]);
@@ -401,6 +397,68 @@ __device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* _
     }
 }
 
+// Double-float residual pass on the 8^3 tiles (FP32-history): the two halves of the
+// shared halo buffer hold the hi and lo parts of x around the tile (zero outside the
+// grid and on inactive voxels, so no neighbour mask is needed).  Writes r (rounded to
+// FP32) on active voxels and adds |r|^2 (and, on the first pass, |b|^2 in FP64) to the
+// thread's partial sums.
+__device__ __forceinline__ void residual_df_tiled(const CGArgs& a, float4 (*sd)[TH * TH * TH],
+                                                  double& rr_p, double& bb_p, bool first) {
+    const long long UV = (long long)a.U * a.V;
+    const long long M = a.M;
+    for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const int org = a.tiles[tile];
+        load_halo(a, a.xh, sd[0], org);
+        load_halo(a, a.xl, sd[1], org);
+        cp_async_commit();
+        const int x0 = org & 1023, y0 = (org >> 10) & 1023, z0 = org >> 20;
+        long long mv[kVoxPerThread];
+        float dhv[kVoxPerThread], dlv[kVoxPerThread];
+        float4 bhv[kVoxPerThread], blv[kVoxPerThread];
+#pragma unroll
+        for (int v = 0; v < kVoxPerThread; ++v) {
+            const int q = threadIdx.x + v * NT;
+            const int x = x0 + q % TT, y = y0 + (q / TT) % TT, z = z0 + q / (TT * TT);
+            mv[v] = -1;
+            if (x < a.U && y < a.V && z < a.W) {
+                const long long m = (long long)z * UV + (long long)y * a.U + x;
+                dhv[v] = a.diag32[m];
+                if (dhv[v] != 0.f) {
+                    mv[v] = m;
+                    dlv[v] = a.diag_lo[m];
+                    bhv[v] = a.bh[m];
+                    blv[v] = a.bl[m];
+                    if (first) {
+                        const double b0 = a.b[m], b1 = a.b[M + m], b2 = a.b[2 * M + m];
+                        bb_p += b0 * b0 + b1 * b1 + b2 * b2;
+                    }
+                }
+            }
+        }
+        cp_async_wait0();
+        __syncthreads();
+#pragma unroll
+        for (int v = 0; v < kVoxPerThread; ++v) {
+            if (mv[v] < 0) continue;
+            const int q = threadIdx.x + v * NT;
+            const int hc = ((q / (TT * TT) + 1) * TH + ((q / TT) % TT + 1)) * TH + (q % TT + 1);
+            auto load = [&](auto e, float* sh, float* sl) {
+                constexpr int E = decltype(e)::value;
+                constexpr int off = ((E / 9 - 1) * TH + ((E / 3) % 3 - 1)) * TH + (E % 3 - 1);
+                const float4 vh = sd[0][hc + off], vl = sd[1][hc + off];
+                df_add(sh[0], sl[0], vh.x, vl.x);
+                df_add(sh[1], sl[1], vh.y, vl.y);
+                df_add(sh[2], sl[2], vh.z, vl.z);
+            };
+            const float4 r = residual_df_at<true>(sd[0][hc], sd[1][hc], dhv[v], dlv[v], bhv[v],
+                                                  blv[v], load, 0);
+            rr_p += (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
+            a.r[mv[v]] = r;
+        }
+        __syncthreads();
+    }
+}
+
 // block-wide sum of two values; result valid in every thread
 __device__ __forceinline__ void block_sum2(double& a, double& b) {
     __shared__ double sh[2][NT / 32];
@@ -448,6 +506,7 @@ __device__ __forceinline__ double grid_total(const double* red, int nb) {
 template <bool DF>
 __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) {
     cg::grid_group grid = cg::this_grid();
+    __shared__ float4 sd[2][TH * TH * TH];        // tile halos of the tiled passes
     const long long M = a.M;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gs = (long long)gridDim.x * blockDim.x;
@@ -478,17 +537,14 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
     while (true) {
         // ---- residual (FP64, or double-float rounded to FP32)
         double rr_p = 0.0, bb_p = 0.0;
-        for (long long i = t0; i < a.nact; i += gs) {
+        if (DF) residual_df_tiled(a, sd, rr_p, bb_p, first);
+        for (long long i = t0; !DF && i < a.nact; i += gs) {
             const int m = a.act[i];
             if (first) {
                 const double b0 = a.b[m], b1 = a.b[M + m], b2 = a.b[2 * M + m];
                 bb_p += b0 * b0 + b1 * b1 + b2 * b2;
             }
-            if (DF) {
-                const float4 r = residual_df(a, m, a.nmask[i]);
-                rr_p += (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
-                a.r[m] = r;
-            } else {
+            {
                 double o[3];
                 applyA64(a, a.x, m, a.nmask[i], o);
                 const double r0 = a.b[m] - o[0], r1 = a.b[M + m] - o[1], r2 = a.b[2 * M + m] - o[2];
@@ -544,7 +600,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         float4* dk = a.p;
         float4* dn = a.q;
         for (int k = 0; k < n_it; ++k) {
-            cheb_pass_tiled(a, dk, dn, a.c1[k], a.c2[k]);
+            cheb_pass_tiled(a, dk, dn, a.c1[k], a.c2[k], sd);
             grid.sync();
             float4* t = dk; dk = dn; dn = t;
         }
