@@ -16,9 +16,9 @@ Contents (each function cites the passage of the paper it follows):
                     Cartesian tensor-Gauss/Duffy route; used only to pin the table
 * ``excitation``    tested incident field (Eq. E) for the modulated Gaussian plane wave
 * ``march``         direct space-time sum (Eq. PnMOT) + dense Z_0 solve (Eq. MOTInversion)
-* ``pdsa``          PDSA matrices D_n (Eq. Dn) and the FIR regularisation identity
-* ``fftconv``       plain-numpy Toeplitz-to-circulant product (App. A), used to pin the
-                    circulant embedding rule, not the CUDA path
+* ``pdsa``          PDSA matrices D_n (Eq. Dn), the FIR regularisation identity, and the
+                    spectrum bracket of D_n from its circulant embedding (App. A; numpy
+                    FFT of the embedded kernel, 3x3 eigenvalues per bin)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against closed
 forms, sum rules, exact identities or brute force, except the absolute physical

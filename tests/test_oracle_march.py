@@ -118,6 +118,86 @@ def test_pdsa_binomials_and_fir_identity():
     assert all(m > 0 for m in mins)          # a 2^3 cube is well inside the PD regime
 
 
+def _pdsa_case(N, seed, n_inactive=2):
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, ell + 1)
+    rng = np.random.default_rng(seed)
+    eps = 2.0 + 9.0 * rng.uniform(size=(N, N, N))
+    eps[0, 0, :n_inactive] = 1.0
+    return ell, G, eps
+
+
+def test_pdsa_circulant_embedding_pins():
+    """Circulant embedding of sum_i c_i G_i on a torus P >= 2N - 1 (App. A): restricted
+    to the grid it is the dense Toeplitz matrix sum_i c_i G_i built by dense_G; its
+    eigenvalues (3x3 blocks of the FFT) are those of the dense circulant matrix built
+    entry by entry; and min a - max eig <= lambda(A_n) <= max a - min eig for a
+    heterogeneous grid with inactive voxels (Weyl + Cauchy interlacing)."""
+    N = 3
+    ell, G, eps = _pdsa_case(N, 11)
+    taps = wl.fir_taps("fir3", 0.05)
+    P = (6, 8, 6)
+    Pu, Pv, Pw = P
+    pw, pv, pu = np.meshgrid(np.arange(Pw), np.arange(Pv), np.arange(Pu), indexing="ij")
+    tor = np.stack([pu.ravel(), pv.ravel(), pw.ravel()], axis=1)        # torus points
+    on_grid = np.nonzero((tor < N).all(axis=1))[0]
+    for n in (0, 3, ell):
+        c = pdsa.pdsa_coefficients(ell, n)
+        K = pdsa.circulant_embedding(G, c, eps.shape, P)
+        d = (tor[:, None, :] - tor[None, :, :]) % np.array([Pu, Pv, Pw])
+        Cd = K[:, :, d[..., 2], d[..., 1], d[..., 0]].transpose(2, 0, 3, 1).reshape(
+            3 * len(tor), 3 * len(tor))
+        rows = (3 * on_grid[:, None] + np.arange(3)).reshape(-1)
+        T = sum(c[i] * march.dense_G(G, i, N, N, N) for i in range(n + 1))
+        assert np.abs(Cd[np.ix_(rows, rows)] - T).max() <= 1e-15 * np.abs(T).max()
+        ev_fft = np.sort(pdsa.circulant_symbol_eigs(K).reshape(-1))
+        ev_dense = np.linalg.eigvalsh(Cd)
+        assert np.abs(ev_fft - ev_dense).max() <= 1e-12 * np.abs(ev_dense).max()
+        lam = np.linalg.eigvalsh(pdsa.scaled_pdsa_matrix(G, eps, taps, ell, n))
+        lo, hi, smin, smax = pdsa.circulant_bounds(G, eps, taps, ell, n, P)
+        assert lo <= lam.min() + 1e-12 and lam.max() <= hi + 1e-12
+        assert smin == ev_fft[0] and smax == ev_fft[-1]
+
+
+def test_pdsa_scaled_operator_pins():
+    """A_n = diag(1/chi) D_n / C(ell, n) on the active voxels: its off-diagonal part is
+    -sum_i c_i G_i and its diagonal a_m = sum_i c_i (T(i)/(eps_m - 1) + delta_i/chi_m)
+    (Eq. Z); D_ell = Z(z = -1) gives a = delta / chi for the FIR taps (T(0) = T(1));
+    the circulant product equals the dense product, and rounding each lag spectrum to
+    float32 moves it by no more than sum_i |c_i| 2^-24 max_k ||Khat_i(k)||_F ||x||."""
+    N = 4
+    ell, G, eps = _pdsa_case(N, 12)
+    taps = wl.fir_taps("fir3", 0.05)
+    act = eps.reshape(-1) > 1.0
+    e = eps.reshape(-1)[act]
+    chi = (e - 1.0) / e
+    P = (8, 8, 8)
+    x = np.random.default_rng(3).normal(size=(N ** 3, 3))
+    for n in (0, 1, 5, ell):
+        A = pdsa.scaled_pdsa_matrix(G, eps, taps, ell, n)
+        c = pdsa.pdsa_coefficients(ell, n)
+        T = sum(c[i] * march.dense_G(G, i, N, N, N) for i in range(n + 1))
+        rows = (3 * np.nonzero(act)[0][:, None] + np.arange(3)).reshape(-1)
+        off = A + T[np.ix_(rows, rows)]
+        a = pdsa.diagonal_of_scaled(eps, taps, ell, n)
+        assert np.abs(off - np.diag(np.repeat(a, 3))).max() <= 1e-14 * np.abs(A).max()
+        if n == ell:
+            assert np.abs(a - 0.05 / chi).max() <= 1e-14 * np.abs(a).max()
+        y = pdsa.circulant_apply(G, eps, taps, ell, n, P, x)
+        yd = np.zeros_like(x)
+        yd[act] = (A @ x[act].reshape(-1)).reshape(-1, 3)
+        assert np.abs(y - yd).max() <= 1e-13 * np.abs(yd).max()
+        y32 = pdsa.circulant_apply(G, eps, taps, ell, n, P, x, round32=True)
+        bound = 0.0
+        for i in range(1, n + 1):
+            one = np.zeros(i + 1)
+            one[i] = 1.0
+            Ki = np.fft.fftn(pdsa.circulant_embedding(G, one, eps.shape, P), axes=(2, 3, 4)).real
+            bound += abs(c[i]) * 2.0 ** -24 * np.sqrt((Ki ** 2).sum(axis=(0, 1))).max()
+        dy = np.linalg.norm(y32 - y)
+        assert dy <= bound * np.linalg.norm(x[act]) and (n == 0 or dy > 0)
+
+
 def test_fir_taps_against_paper():
     """Eqs. FIR2-FIR4 as printed (FIR4 last tap per reading R7), Eq. RegReq1, and the
     magnitude (Eq. FIRmagnitude) of the 9-tap binomial member of the family in closed
