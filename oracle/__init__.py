@@ -19,6 +19,8 @@ Contents (each function cites the passage of the paper it follows):
 * ``pdsa``          PDSA matrices D_n (Eq. Dn), the FIR regularisation identity, and the
                     spectrum bracket of D_n from its circulant embedding (App. A; numpy
                     FFT of the embedded kernel, 3x3 eigenvalues per bin)
+* ``response``      tapered frequency response |H^alpha| (Eq. Halpha) and the incident
+                    pulse's amplitude spectrum
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against closed
 forms, sum rules, exact identities or brute force, except the absolute physical

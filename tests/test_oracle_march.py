@@ -285,3 +285,34 @@ def test_adjoint_gradient_matches_finite_differences():
         em[m] -= h
         fd = (objective(ep.reshape(eps_r.shape)) - objective(em.reshape(eps_r.shape))) / (2 * h)
         assert abs(fd - grad[m]) < 1e-6 * max(abs(fd), 1e-3 * np.abs(grad).max())
+
+
+def test_response_pins():
+    """Tapered DFT and the incident spectrum (Eq. Halpha): a cosine on a DFT bin gives
+    N dt / 2 there and 0 on the other bins without taper; a constant series gives
+    dt (n_flat + (T - 1) / 2) at f = 0 with a T-sample half-cosine taper; |e^i(f)|
+    equals the FFT of the densely sampled pulse."""
+    from oracle import response
+    N, dt = 240, 0.5
+    t = dt * np.arange(1, N + 1)
+    k0 = 17
+    J = np.cos(2 * np.pi * k0 / (N * dt) * t)[:, None]
+    f = np.arange(0, N // 2) / (N * dt)
+    jf = np.abs(response.tapered_dft(J, dt, 0.0, f))[:, 0]
+    assert abs(jf[k0] - N * dt / 2) < 1e-10
+    assert np.delete(jf, k0).max() < 1e-10
+    w = response.taper_weights(N, 0.2)
+    T = int(np.floor(0.2 * N))
+    assert abs(w.sum() - ((N - T) + (T - 1) / 2)) < 1e-12
+    assert w[N - T - 1] == 1.0 and abs(w[-1]) < 1e-15
+    one = np.ones((N, 1))
+    assert abs(response.tapered_dft(one, dt, 0.2, [0.0])[0, 0] - dt * w.sum()) < 1e-12
+    fc, st = 0.03, 20.0
+    h = 0.25
+    ts = h * np.arange(-4000, 4000)
+    x = np.sin(2 * np.pi * fc * ts) * np.exp(-ts ** 2 / (2 * st ** 2))
+    X = h * np.abs(np.fft.fft(x))
+    fr = np.fft.fftfreq(ts.size, h)
+    sel = (fr >= 0) & (fr < 0.1)
+    ref = response.incident_amplitude(fr[sel], fc, st)
+    assert np.abs(X[sel] - ref).max() < 1e-10 * ref.max()
