@@ -253,6 +253,114 @@ mot_status mot_get_table(mot_ctx* ctx, int l0, int n_lags, double* out);
  */
 mot_status mot_get_spectrum(mot_ctx* ctx, int l, double* out);
 
+/*
+ * Positive definite stability analysis (Sec. 5.1, Eq. Dn).  The PDSA matrices
+ *     D_n = sum_{i=0}^{n} (-1)^i C(ell - i, n - i) Z_i,   n = 0..ell,
+ * (D_0 = Z_0, D_ell = sum_i (-1)^i Z_i = Z(z = -1)) all positive definite keep every
+ * companion-matrix eigenvalue on the negative real axis inside the unit circle.  The
+ * functions below work on the scaled operator
+ *     A_n = diag(1/chi) D_n / C(ell, n)
+ * restricted to the active voxels (eps_r > 1; the other rows only hold their own
+ * diagonal and a current that stays zero).  A_n is symmetric and has the signs of
+ * D_n's eigenvalues; its Z_i include this context's FIR taps (Sec. 6.1), so
+ * D_ell^delta = D_ell + delta I (Eq. Regularization) is analysed by creating the
+ * context with the taps.  The Toeplitz part sum_i c_i G_i is applied as one spatial
+ * FFT convolution on the padded grid (App. A).  FP64 contexts only (MOT_ERR_ARG
+ * otherwise); the context's stream is used and the calls are synchronous.  The
+ * operator of the last (n, flags) is cached in the context (a [noct][6] FP64 kernel
+ * spectrum, an [M] diagonal and FFT scratch, freed by mot_destroy).
+ *  n      0 <= n <= ell
+ *  flags  0, or MOT_PDSA_FP32_SPECTRUM: every lag's spectrum Ghat_i (i >= 1) is
+ *         rounded to FP32 before it is summed, as the FP32-history direct scheme
+ *         multiplies it, so the analysis includes that finite-precision error
+ *         (the perturbation N of Eq. DellFinitePrecision)
+ * Errors: MOT_ERR_ARG (bad n, flags, pointer, precision), MOT_ERR_OOM, MOT_ERR_CUDA.
+ */
+#define MOT_PDSA_FP32_SPECTRUM 1
+
+/*
+ * mot_pdsa_apply - y = A_n x.
+ *  x, y  [M][3] doubles, host or device; entries of voxels with eps_r = 1 are ignored
+ *        in x and returned 0 in y
+ */
+mot_status mot_pdsa_apply(mot_ctx* ctx, int n, int flags, const double* x, double* y);
+
+/*
+ * mot_pdsa_bounds - rigorous bracket of the spectrum of A_n from the circulant
+ * embedding of its Toeplitz part (Weyl's inequality and Cauchy interlacing):
+ *  out  host pointer, 5 doubles: [0] lower bound of lambda_min(A_n), [1] upper bound
+ *       of lambda_max(A_n), [2] min and [3] max eigenvalue of the 3x3 blocks of the
+ *       padded kernel spectrum, [4] the largest chi over active voxels
+ * A positive out[0] proves D_n positive definite; a negative one decides nothing.
+ */
+mot_status mot_pdsa_bounds(mot_ctx* ctx, int n, int flags, double out[5]);
+
+/*
+ * mot_pdsa_lanczos - extreme eigenvalues of A_n by k Lanczos steps on the device from
+ * a start vector drawn from `seed`.
+ *  flags   MOT_PDSA_FP32_SPECTRUM as above; MOT_PDSA_FULL_REORTH keeps the basis and
+ *          reorthogonalises every step against it (device memory (k + 1) 3M doubles),
+ *          else the plain three-term recurrence runs (memory 4 x 3M doubles; k may
+ *          exceed the dimension: lost orthogonality only repeats converged Ritz values)
+ *  k       steps (>= 1); fewer are taken when the Krylov space becomes invariant
+ *  n_out   how many of the smallest Ritz values to return in ritz (ascending)
+ *  ritz    host pointer, n_out doubles (may be NULL when n_out = 0)
+ *  info    host pointer, 2 ints: [0] Ritz values written, [1] steps taken
+ *  extreme host pointer, 4 doubles: smallest Ritz value, its residual norm
+ *          ||A y - theta y||, largest Ritz value, its residual norm; each lies within
+ *          its residual of an eigenvalue of A_n
+ * The smallest Ritz value is an upper bound of lambda_min(A_n) (to rounding of order
+ * k eps ||A_n|| without reorthogonalisation): a clearly negative value proves that D_n
+ * is not positive definite.
+ */
+#define MOT_PDSA_FULL_REORTH 2
+mot_status mot_pdsa_lanczos(mot_ctx* ctx, int n, int flags, int k, unsigned long long seed,
+                            int n_out, double* ritz, int info[2], double extreme[4]);
+
+/*
+ * mot_truncate_table - the truncated MOT-JVIE of the finite-precision experiment
+ * (Sec. 6): every tabulated element G_l^{ab}(d) of a history lag l >= 1 is replaced
+ * by the nearest multiple of eps_trunc (ties to even) and the spectra derived from the
+ * table are recomputed.  The lag-0 elements (the stencil of the Z_0 solve) are kept.
+ * Call on a fresh context (no step marched, not created by or shared with
+ * mot_create_shared).
+ * Errors: MOT_ERR_ARG (eps_trunc not finite and > 0, context marched or shared),
+ *         MOT_ERR_CUDA.
+ */
+mot_status mot_truncate_table(mot_ctx* ctx, double eps_trunc);
+
+/*
+ * mot_fir_magnitude - FIR-regularisation magnitude |sum_n exp(-i n theta) delta_n|
+ * (Eq. FIRmagnitude) of the taps delta_0..delta_{n_taps-1} at n_theta normalised
+ * frequencies theta (host arrays; out host, n_theta doubles).  Host computation, no
+ * device use.  Errors: MOT_ERR_ARG (negative counts, NULL arrays).
+ */
+mot_status mot_fir_magnitude(const double* taps, int n_taps, int n_theta, const double* theta,
+                             double* out);
+
+/*
+ * mot_frequency_response - |H^alpha|(r, f) of Eq. Halpha at n_probe probe voxels from
+ * their time series, on the device (Sec. 7.1).  The series J_n (n = 1..n_steps, time
+ * t_n = n dt) is tapered by a half cosine over its last fraction `taper` (the samples
+ * n > n_steps - floor(taper n_steps) weigh 0.5 (1 + cos(pi (n - n_flat) / (n_steps -
+ * n_flat)))), transformed as j(f) = dt sum_n w_n J_n exp(-2 pi i f t_n), and divided by
+ * (eps_r - 1) |e^i(f)| with the amplitude spectrum of the modulated Gaussian pulse
+ * sin(2 pi f_c tau) exp(-tau^2 / (2 sigma_t^2)) (eps0 = c0 = 1):
+ *     |e^i(f)| = sigma_t sqrt(2 pi) / 2 |exp(-2 pi^2 sigma_t^2 (f - f_c)^2)
+ *                                       - exp(-2 pi^2 sigma_t^2 (f + f_c)^2)|.
+ *  J          [n_steps][n_probe][3] doubles, host or device
+ *  taper      in [0, 1)
+ *  eps_probe  host, n_probe values of eps_r (> 1) at the probes
+ *  freqs      host, n_freq frequencies (cycles per unit time, c0 = h = 1)
+ *  H          host, [n_freq][n_probe][3] doubles
+ *  j_hat      host or NULL, [n_freq][n_probe][3] complex (re, im) doubles
+ * Synchronous on the default stream.  Errors: MOT_ERR_ARG, MOT_ERR_OOM, MOT_ERR_CUDA.
+ */
+mot_status mot_frequency_response(int n_steps, int n_probe, const double* J, double dt,
+                                  double taper, const double* eps_probe, double f_c,
+                                  double sigma_t, int n_freq, const double* freqs, double* H,
+                                  double* j_hat);
+
 /* Grid facts and the last march's diagnostics.  Any pointer may be NULL.
  *  ell, P[3]            lags and padded FFT sizes
  *  n_done               steps marched so far

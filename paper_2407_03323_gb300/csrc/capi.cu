@@ -89,6 +89,10 @@ void free_all(mot_ctx* c) {
     cudaFree(c->tiles);
     cudaFree(c->diag32);
     cudaFree(c->vfac);
+    cudaFree(c->pdsa_spec);
+    cudaFree(c->pdsa_a);
+    cudaFree(c->pdsa_xhat);
+    cudaFree(c->pdsa_conv);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
     if (c->stream) cudaStreamDestroy(c->stream);

@@ -144,6 +144,13 @@ struct mot_ctx {
     int adj_done = 0;            //   adjoint steps done (tau)
     double* adj_gchi = nullptr;  //   dO/dchi accumulated so far (device, [M])
 
+    // PDSA operator A_n (pdsa.cu): kernel spectrum and diagonal of the last (n, flags)
+    double* pdsa_spec = nullptr;   // [noct][6] unnormalised spectrum of sum_i c_i G_i
+    double* pdsa_a = nullptr;      // [M] diagonal a_m (0 on voxels with chi = 0)
+    double2* pdsa_xhat = nullptr;  // [3][nbins] spectrum scratch
+    double* pdsa_conv = nullptr;   // [3][M] convolution scratch
+    int pdsa_n = -1, pdsa_flags = -1;
+
     // counters and optional phase timing
     mot_stats stats = {};
     bool profiling = false;
@@ -175,6 +182,8 @@ void compute_table(mot_ctx* c);
 // spectra.cu
 void compute_spectra(mot_ctx* c);
 void spectrum_of_lag(mot_ctx* c, int l, double* host_out);
+void spectrum_of_combination(mot_ctx* c, const double* w_host, int n, bool round32,
+                             double* dst);
 // fft.cu
 void fft_plan_axis(AxisFFT& a, int P);
 void fft_free_axis(AxisFFT& a);

@@ -36,6 +36,32 @@ __global__ void extract_lag_kernel(const int* __restrict__ tab_l0, const double*
     g[i] = (idx >= 0 && idx < mot::WIN) ? tab[(i * 6 + cc) * mot::WIN + idx] : 0.0;
 }
 
+// g[d] = sum_{l <= n} w[l] G_l(d) for component cc (the lags of the window at d)
+__global__ void extract_weighted_kernel(const int* __restrict__ tab_l0,
+                                        const double* __restrict__ tab, long long noff,
+                                        const double* __restrict__ w, int n, int cc,
+                                        double* __restrict__ g) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= noff) return;
+    const int l0 = tab_l0[i];
+    double acc = 0.0;
+    for (int k = 0; k < mot::WIN && l0 + k <= n; ++k)
+        if (l0 + k >= 0) acc = fma(w[l0 + k], tab[(i * 6 + cc) * mot::WIN + k], acc);
+    g[i] = acc;
+}
+
+// dst[o][cc] += w * src[cc][o], src optionally rounded to FP32 first
+__global__ void accum_kernel(const double* __restrict__ src, long long noct, double w,
+                             int round32, double* __restrict__ dst) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * noct) return;
+    const long long o = i / 6;
+    const int cc = (int)(i % 6);
+    double v = src[cc * noct + o];
+    if (round32) v = (double)(float)v;
+    dst[i] = fma(w, v, dst[i]);
+}
+
 // out[o2][o1][k] = sum_{d < n} in[o2][o1][d] * w[d][k]         (transform along the fastest axis)
 __global__ void pass_fast(const double* __restrict__ in, int n, long long nrows,
                           const double* __restrict__ w, int K, double* __restrict__ out) {
@@ -102,13 +128,11 @@ struct Scratch {
 // odd axes of component cc (order xx, yy, zz, xy, xz, yz): bit a set if odd along a
 const int kOddMask[6] = {0, 0, 0, 3, 5, 6};
 
-void spectrum_one(mot_ctx* c, const TrigTables& tt, Scratch& sc, int l, int cc, double* dst) {
+// spectrum of the octant kernel sc.g (component cc) into dst [noct]
+void transform_one(mot_ctx* c, const TrigTables& tt, Scratch& sc, int cc, double* dst) {
     const int U = c->U, V = c->V, W = c->W;
     const int Hu = c->Hu, Hv = c->Hv, Hw = c->Hw;
-    const long long noff = (long long)U * V * W;
     cudaStream_t s = c->stream;
-    extract_lag_kernel<<<nblk(noff, 256), 256, 0, s>>>(c->tab_l0, c->tab, noff, l, cc, sc.g);
-    MOT_LAUNCH_CHECK();
     const int odd = kOddMask[cc];
     const double* wx = (odd & 1) ? tt.sinw[0] : tt.cosw[0];
     const double* wy = (odd & 2) ? tt.sinw[1] : tt.cosw[1];
@@ -126,6 +150,14 @@ void spectrum_one(mot_ctx* c, const TrigTables& tt, Scratch& sc, int l, int cc, 
         store_kernel<double><<<nblk(c->noct, 256), 256, 0, s>>>(dst, c->noct, -1.0, dst);
         MOT_LAUNCH_CHECK();
     }
+}
+
+void spectrum_one(mot_ctx* c, const TrigTables& tt, Scratch& sc, int l, int cc, double* dst) {
+    const long long noff = (long long)c->U * c->V * c->W;
+    extract_lag_kernel<<<nblk(noff, 256), 256, 0, c->stream>>>(c->tab_l0, c->tab, noff, l, cc,
+                                                              sc.g);
+    MOT_LAUNCH_CHECK();
+    transform_one(c, tt, sc, cc, dst);
 }
 
 void make_tables(mot_ctx* c, TrigTables& tt) {
@@ -196,6 +228,56 @@ void spectrum_of_lag(mot_ctx* c, int l, double* host_out) {
         throw;
     }
     cudaFree(tmp);
+}
+
+
+// dst [noct][6] (FP64, unnormalised) = spectrum of sum_{l=0}^{n} w_l G_l.  Without
+// round32 the weighted kernel is combined in space and transformed once; with round32
+// every lag l >= 1 is transformed alone and rounded to FP32 before it is weighted (the
+// per-lag spectra the FP32-history direct scheme multiplies; lag 0 stays FP64, as in
+// the Z_0 solve).
+void spectrum_of_combination(mot_ctx* c, const double* w_host, int n, bool round32,
+                             double* dst) {
+    TrigTables tt;
+    Scratch sc;
+    make_tables(c, tt);
+    make_scratch(c, sc);
+    double* tmp = nullptr;
+    double* w = nullptr;
+    const long long noff = (long long)c->U * c->V * c->W;
+    cudaStream_t s = c->stream;
+    try {
+        MOT_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * c->noct * 6));
+        MOT_CUDA_TRY(cudaMalloc(&w, sizeof(double) * (n + 1)));
+        MOT_CUDA_TRY(cudaMemcpyAsync(w, w_host, sizeof(double) * (n + 1),
+                                     cudaMemcpyHostToDevice, s));
+        if (!round32) {
+            for (int cc = 0; cc < 6; ++cc) {
+                extract_weighted_kernel<<<nblk(noff, 256), 256, 0, s>>>(c->tab_l0, c->tab, noff,
+                                                                       w, n, cc, sc.g);
+                MOT_LAUNCH_CHECK();
+                transform_one(c, tt, sc, cc, tmp + cc * c->noct);
+            }
+            interleave_kernel<double><<<nblk(6 * c->noct, 256), 256, 0, s>>>(tmp, c->noct, dst);
+            MOT_LAUNCH_CHECK();
+        } else {
+            MOT_CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(double) * 6 * c->noct, s));
+            for (int l = 0; l <= n; ++l) {
+                if (w_host[l] == 0.0) continue;
+                for (int cc = 0; cc < 6; ++cc) spectrum_one(c, tt, sc, l, cc, tmp + cc * c->noct);
+                accum_kernel<<<nblk(6 * c->noct, 256), 256, 0, s>>>(tmp, c->noct, w_host[l],
+                                                                    l >= 1, dst);
+                MOT_LAUNCH_CHECK();
+            }
+        }
+        MOT_CUDA_TRY(cudaStreamSynchronize(s));
+    } catch (...) {
+        cudaFree(tmp);
+        cudaFree(w);
+        throw;
+    }
+    cudaFree(tmp);
+    cudaFree(w);
 }
 
 }  // namespace mot

@@ -31,7 +31,11 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_plane_wave_static", "mot_march", "mot_restart", "mot_adjoint_begin",
            "mot_adjoint_run", "mot_adjoint_end",
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
-           "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_last_error"]
+           "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
+           "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
+           "mot_frequency_response", "mot_last_error"]
+MOT_PDSA_FP32_SPECTRUM = 1
+MOT_PDSA_FULL_REORTH = 2
 
 
 class Stats(ctypes.Structure):
@@ -83,6 +87,12 @@ def load_library(path=LIB_PATH):
     lib.mot_set_solver.argtypes = [P, D, I, D]
     lib.mot_set_profiling.argtypes = [P, I]
     lib.mot_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+    lib.mot_pdsa_apply.argtypes = [P, I, I, P, P]
+    lib.mot_pdsa_bounds.argtypes = [P, I, I, P]
+    lib.mot_pdsa_lanczos.argtypes = [P, I, I, I, ctypes.c_ulonglong, I, P, P, P]
+    lib.mot_truncate_table.argtypes = [P, D]
+    lib.mot_fir_magnitude.argtypes = [P, I, I, P, P]
+    lib.mot_frequency_response.argtypes = [I, I, P, D, D, P, D, D, I, P, P, P]
     lib.mot_last_error.argtypes = [P]
     lib.mot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -122,6 +132,40 @@ def _dtype_ok(buf):
         return buf.dtype == np.float64
     dt = getattr(buf, "dtype", None)
     return dt is None or str(dt) == "torch.float64"
+
+
+def fir_magnitude(taps, theta):
+    """|sum_n exp(-i n theta) delta_n| (Eq. FIRmagnitude) at the normalised frequencies
+    theta (mot_fir_magnitude)."""
+    lib = load_library()
+    t = np.ascontiguousarray(taps, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1)
+    out = np.zeros_like(th)
+    st = lib.mot_fir_magnitude(t.ctypes.data if t.size else None, t.size, th.size,
+                               th.ctypes.data, out.ctypes.data)
+    if st != MOT_OK:
+        raise MotError(st, "mot_fir_magnitude: invalid arguments")
+    return out
+
+
+def frequency_response(J, dt, taper, eps_probe, f_c, sigma_t, freqs, with_spectrum=False):
+    """|H^alpha|(r, f) of Eq. Halpha from probe series J [N][n_probe][3] (numpy or CUDA
+    tensor; mot_frequency_response): tapered over the last fraction `taper`, returns
+    H [n_freq][n_probe][3] (and the complex j(f) with with_spectrum)."""
+    lib = load_library()
+    if isinstance(J, np.ndarray):
+        J = np.ascontiguousarray(J, dtype=np.float64)
+    n_steps, n_probe = J.shape[0], J.shape[1]
+    e = np.ascontiguousarray(eps_probe, dtype=np.float64).reshape(-1)
+    f = np.ascontiguousarray(freqs, dtype=np.float64).reshape(-1)
+    H = np.zeros((f.size, n_probe, 3))
+    jh = np.zeros((f.size, n_probe, 3), dtype=np.complex128) if with_spectrum else None
+    st = lib.mot_frequency_response(n_steps, n_probe, _ptr(J), dt, taper, e.ctypes.data, f_c,
+                                    sigma_t, f.size, f.ctypes.data, H.ctypes.data,
+                                    None if jh is None else jh.ctypes.data)
+    if st != MOT_OK:
+        raise MotError(st, "mot_frequency_response failed")
+    return (H, jh) if with_spectrum else H
 
 
 class Context:
@@ -300,6 +344,47 @@ class Context:
         out = np.zeros((6, Pw // 2 + 1, Pv // 2 + 1, Pu // 2 + 1))
         self._check(self._lib.mot_get_spectrum(self._h, l, out.ctypes.data))
         return out
+
+    def truncate_table(self, eps_trunc):
+        """Round every element of the history lags l >= 1 to a multiple of eps_trunc
+        (mot_truncate_table; before the first step)."""
+        self._check(self._lib.mot_truncate_table(self._h, float(eps_trunc)))
+
+    # ---------------------------------------------------------------- PDSA (Eq. Dn)
+    def pdsa_apply(self, n, x, out=None, fp32_spectrum=False):
+        """y = A_n x, A_n = diag(1/chi) D_n / C(ell, n) on the active voxels
+        (mot_pdsa_apply); x, out [M][3] float64, numpy or CUDA tensor."""
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        if out is None:
+            out = np.zeros((self.M, 3))
+        flags = MOT_PDSA_FP32_SPECTRUM if fp32_spectrum else 0
+        self._check(self._lib.mot_pdsa_apply(self._h, n, flags, _ptr(x), _ptr(out)))
+        return out
+
+    def pdsa_bounds(self, n, fp32_spectrum=False):
+        """Rigorous bracket of the spectrum of A_n from the circulant embedding
+        (mot_pdsa_bounds)."""
+        out = np.zeros(5)
+        flags = MOT_PDSA_FP32_SPECTRUM if fp32_spectrum else 0
+        self._check(self._lib.mot_pdsa_bounds(self._h, n, flags, out.ctypes.data))
+        return {"lo": out[0], "hi": out[1], "symbol_min": out[2], "symbol_max": out[3],
+                "chi_max": out[4]}
+
+    def pdsa_lanczos(self, n, k, seed=0, fp32_spectrum=False, reorth=False, n_out=8):
+        """k Lanczos steps on A_n (mot_pdsa_lanczos): the n_out smallest Ritz values
+        (ascending), the extreme Ritz values with their residual norms, steps taken."""
+        ritz = np.zeros(max(n_out, 1))
+        info = (ctypes.c_int * 2)()
+        ext = np.zeros(4)
+        flags = (MOT_PDSA_FP32_SPECTRUM if fp32_spectrum else 0) | \
+                (MOT_PDSA_FULL_REORTH if reorth else 0)
+        self._check(self._lib.mot_pdsa_lanczos(self._h, n, flags, k, seed, n_out,
+                                               ritz.ctypes.data,
+                                               ctypes.cast(info, ctypes.c_void_p),
+                                               ext.ctypes.data))
+        return {"ritz": ritz[:info[0]].copy(), "theta_min": ext[0], "resid_min": ext[1],
+                "theta_max": ext[2], "resid_max": ext[3], "steps": info[1]}
 
     @property
     def levels(self):

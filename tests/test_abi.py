@@ -61,3 +61,15 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
                         1.0, ctypes.cast(eps, ctypes.c_void_p), None, 0, 0, 0, 0,
                         ctypes.byref(out))
     assert st == 1 and b"eps_r" in lib.mot_last_error(None)
+
+
+def test_fir_magnitude_host_call(lib):
+    """mot_fir_magnitude is host-only: the FIR2/3/4 taps of Sec. 6.2 (FIR4 per reading
+    R7) have the magnitudes delta sin^k(theta / 2), k = 1, 2, 3 (Eq. FIRmagnitude)."""
+    import numpy as np
+    import workloads as wl
+    from paper_2407_03323_gb300 import mot
+    th = np.linspace(0.0, np.pi, 41)
+    for k, name in ((1, "fir2"), (2, "fir3"), (3, "fir4")):
+        mag = mot.fir_magnitude(wl.fir_taps(name, 0.1), th)
+        assert np.abs(mag - 0.1 * np.sin(th / 2) ** k).max() < 1e-15
