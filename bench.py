@@ -178,6 +178,28 @@ def profile_traffic(config, precision, scheme, kernel):
     return None
 
 
+# ------------------------------------------------------------------ replicas
+
+def max_over_ranks(x, world):
+    """The largest of the ranks' values (each rank times its own replica between
+    barriers; the slowest one bounds the job).  Works on any initialised process group:
+    NCCL reduces a device tensor, gloo a host one."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, seconds, world):
+    """Whole-job rate: every rank marches the same workload (weak scaling, replicas),
+    so the job processes world * units in the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ our arm
 
 def march_timed(ctx, torch, stream, E, n_steps, dev, world):
@@ -194,11 +216,7 @@ def march_timed(ctx, torch, stream, E, n_steps, dev, world):
         ctx.march(n_steps, out=None, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     return ms, clk.summary()
 
 
@@ -250,7 +268,7 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
     out = {
         "scheme": scheme, "block": block if scheme == "blocked" else None,
         "time_steps_per_bench_step": per,
-        "value": world * M * n_time / (ms * 1e-3),
+        "value": job_throughput(M * n_time, ms * 1e-3, world),
         "ms_per_step": ms / steps, "ms_per_time_step": ms / n_time,
         "setup_s": setup_s, "launches": st["launches"],
         "cg_inner_iters_per_time_step": st["cg_iters"] / max(st["steps"], 1),
@@ -278,12 +296,8 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
         ctx.set_excitation(Eh, stream=stream)
         ctx.march(k, out=Jh, stream=stream)
         torch.cuda.synchronize()
-        sec = time.perf_counter() - t_0
-        if world > 1:
-            t = torch.tensor([sec], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            sec = float(t.item())
-        e2e = {"value": world * M * k / sec, "unit": "voxel-timesteps/s",
+        sec = max_over_ranks(time.perf_counter() - t_0, world)
+        e2e = {"value": job_throughput(M * k, sec, world), "unit": "voxel-timesteps/s",
                "h2d_bytes_per_step": M * 3 * 8 * per, "d2h_bytes_per_step": M * 3 * 8 * per,
                "variant": "%s/%s" % (prec, scheme)}
     ctx.close()

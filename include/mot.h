@@ -371,8 +371,8 @@ mot_status mot_get_info(const mot_ctx* ctx, int* ell, int P[3], int* n_done,
                         double* last_norm, int* fail_step, int* last_cg_iters);
 
 /* Set per-step solver/monitor parameters.  tol: the FP64 residual of the Z_0 solve
- * must fall below tol ||rhs / chi|| (default 1e-13 for MOT_FP64, 1e-10 for
- * MOT_FP32_HISTORY, whose history already carries ~1e-7 relative error); max_iter:
+ * must fall below tol ||rhs / chi|| (default 1e-13 for MOT_FP64, 3e-8 for
+ * MOT_FP32_HISTORY, whose history already carries ~2e-7 relative error); max_iter:
  * cap on the inner (FP32) iterations per step (default 200); growth_limit: a step
  * whose ||J_n|| exceeds growth_limit times the largest norm seen so far is reported
  * as MOT_ERR_UNSTABLE (default 1e12). */

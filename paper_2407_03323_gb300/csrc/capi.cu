@@ -93,8 +93,17 @@ void free_all(mot_ctx* c) {
     cudaFree(c->pdsa_a);
     cudaFree(c->pdsa_xhat);
     cudaFree(c->pdsa_conv);
+    cudaFree(c->pw_tab);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     c->events.clear();
+    for (cudaEvent_t e : c->e_chunk) cudaEventDestroy(e);
+    c->e_chunk.clear();
+    for (int k = 0; k < 3; ++k) {
+        if (c->out_ready[k]) cudaEventDestroy(c->out_ready[k]);
+        if (c->out_done[k]) cudaEventDestroy(c->out_done[k]);
+    }
+    if (c->cstream) cudaStreamDestroy(c->cstream);
+    if (c->hstream) cudaStreamDestroy(c->hstream);
     if (c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -112,6 +121,22 @@ void reset_state(mot_ctx* c, cudaStream_t s) {
 void history_for(mot_ctx* c, int n, cudaStream_t s, cudaEvent_t* ev = nullptr) {
     if (c->precision == MOT_FP64) mot::history_step<double>(c, n, s, ev);
     else mot::history_step<float>(c, n, s, ev);
+}
+
+constexpr int kOutSlots = 3;   // output ring depth (host J_out)
+
+void ensure_copy_stream(mot_ctx* c) {
+    if (!c->cstream) MOT_CUDA_TRY(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+}
+
+void ensure_stage_stream(mot_ctx* c) {
+    if (!c->hstream) MOT_CUDA_TRY(cudaStreamCreateWithFlags(&c->hstream, cudaStreamNonBlocking));
+}
+
+cudaEvent_t new_sync_event() {
+    cudaEvent_t e;
+    MOT_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return e;
 }
 
 void ensure_events(mot_ctx* c, size_t n) {
@@ -166,9 +191,11 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
     c->block = block;
     c->n_taps = n_taps;
     c->taps.assign(fir_taps, fir_taps + n_taps);
-    // per-step solve tolerance: the FP32-history variant's history carries ~1e-7 relative
-    // error, so 1e-10 on the FP64 residual is far below it; FP64 solves to 1e-13
-    c->tol = precision == MOT_FP64 ? 1e-13 : 1e-10;
+    // per-step solve tolerance: the FP32-history variant's history P carries ~2e-7
+    // relative error per step (FP32 FFT convolution), so a residual of 3e-8 ||rhs/chi||
+    // stays below it (the FP32-vs-FP64 deviation of the march is the same for 1e-10 ..
+    // 3e-8); FP64 solves to 1e-13
+    c->tol = precision == MOT_FP64 ? 1e-13 : 3e-8;
     // Eq. Ell with h = c dt = 1
     c->ell = (int)std::floor(std::sqrt((double)c->U * c->U + (double)c->V * c->V +
                                        (double)c->W * c->W)) + 2;
@@ -288,6 +315,7 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         if (c->nact) mot::chebyshev_setup(c);
         MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
         MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
+        MOT_CUDA_TRY(cudaMalloc(&c->pw_tab, sizeof(double) * mot::kPwTable));
         reset_state(c, c->stream);
         MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     });
@@ -363,6 +391,7 @@ mot_status mot_create_shared(mot_ctx* src, mot_ctx** out) {
         MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
         MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
         MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
+        MOT_CUDA_TRY(cudaMalloc(&c->pw_tab, sizeof(double) * mot::kPwTable));
         reset_state(c, c->stream);
         MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
     });
@@ -381,6 +410,12 @@ mot_status mot_set_excitation(mot_ctx* c, int n_steps, const double* E, void* st
     if (n_steps < 1 || !E) { c->err = "n_steps >= 1 and E non-null required"; return MOT_ERR_ARG; }
     return guarded(c, [&] {
         cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+        if (c->hstream) {   // a host staging still in flight writes the buffer: order after it
+            cudaEvent_t pending = new_sync_event();
+            MOT_CUDA_TRY(cudaEventRecord(pending, c->hstream));
+            MOT_CUDA_TRY(cudaStreamWaitEvent(s, pending, 0));
+            cudaEventDestroy(pending);
+        }
         if (n_steps > c->E_cap) {
             MOT_CUDA_TRY(cudaStreamSynchronize(s));
             cudaFree(c->Estage);
@@ -389,9 +424,32 @@ mot_status mot_set_excitation(mot_ctx* c, int n_steps, const double* E, void* st
             MOT_CUDA_TRY(cudaMalloc(&c->Estage, sizeof(double) * 3 * c->M * n_steps));
             c->E_cap = n_steps;
         }
-        MOT_CUDA_TRY(cudaMemcpyAsync(c->Estage, E, sizeof(double) * 3 * c->M * n_steps,
-                                     is_device_ptr(E) ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyHostToDevice, s));
+        const long long step = 3 * c->M;
+        if (is_device_ptr(E)) {
+            MOT_CUDA_TRY(cudaMemcpyAsync(c->Estage, E, sizeof(double) * step * n_steps,
+                                         cudaMemcpyDeviceToDevice, s));
+            c->e_chunk_steps = 0;
+        } else {
+            // host source: chunks of ~64 MB on the staging stream, each with an event, so
+            // that mot_march starts on the first steps while the rest still arrives;
+            // the copies wait for work already queued on s (it may read the buffer)
+            ensure_stage_stream(c);
+            const int ch = (int)std::max(1LL, (64LL << 20) / (long long)(sizeof(double) * step));
+            const int nch = (n_steps + ch - 1) / ch;
+            while ((int)c->e_chunk.size() < nch) c->e_chunk.push_back(new_sync_event());
+            cudaEvent_t before = new_sync_event();
+            MOT_CUDA_TRY(cudaEventRecord(before, s));
+            MOT_CUDA_TRY(cudaStreamWaitEvent(c->hstream, before, 0));
+            cudaEventDestroy(before);
+            for (int j = 0; j < nch; ++j) {
+                const long long a = (long long)j * ch, b = std::min<long long>(n_steps, a + ch);
+                MOT_CUDA_TRY(cudaMemcpyAsync(c->Estage + a * step, E + a * step,
+                                             sizeof(double) * step * (b - a),
+                                             cudaMemcpyHostToDevice, c->hstream));
+                MOT_CUDA_TRY(cudaEventRecord(c->e_chunk[j], c->hstream));
+            }
+            c->e_chunk_steps = ch;
+        }
         c->E_first = c->n_done + 1;
         c->E_count = n_steps;
     });
@@ -442,15 +500,31 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
             MOT_CUDA_TRY(cudaMalloc(&c->norms, sizeof(double) * n_steps));
             c->norms_cap = n_steps;
         }
-        if (J_out && !dev_out && !c->outbuf)
-            MOT_CUDA_TRY(cudaMalloc(&c->outbuf, sizeof(double) * 3 * c->M));
+        const long long step = 3 * c->M;
+        if (J_out && !dev_out) {
+            if (!c->outbuf) MOT_CUDA_TRY(cudaMalloc(&c->outbuf, sizeof(double) * step * kOutSlots));
+            ensure_copy_stream(c);
+            for (int k = 0; k < kOutSlots; ++k) {
+                if (!c->out_ready[k]) c->out_ready[k] = new_sync_event();
+                if (!c->out_done[k]) c->out_done[k] = new_sync_event();
+            }
+        }
+        int waited_chunk = -1;
         MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
         if (c->profiling) ensure_events(c, 6 * (size_t)n_steps);
         for (int i = 0; i < n_steps; ++i) {
             const int n = c->n_done + 1 + i;
             const double* En = nullptr;
-            if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count)
-                En = c->Estage + (long long)(n - c->E_first) * 3 * c->M;
+            if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count) {
+                En = c->Estage + (long long)(n - c->E_first) * step;
+                if (c->e_chunk_steps > 0) {   // host excitation still arriving: wait for its chunk
+                    const int j = (n - c->E_first) / c->e_chunk_steps;
+                    if (j != waited_chunk) {
+                        MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->e_chunk[j], 0));
+                        waited_chunk = j;
+                    }
+                }
+            }
             cudaEvent_t* ev = c->profiling ? &c->events[6 * (size_t)i] : nullptr;
             if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
             history_for(c, n, s, ev ? ev + 1 : nullptr);
@@ -463,9 +537,18 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
                 if (dev_out) {
                     mot::write_aos(c, n, dst, s);
                 } else {
-                    mot::write_aos(c, n, c->outbuf, s);
-                    MOT_CUDA_TRY(cudaMemcpyAsync(dst, c->outbuf, sizeof(double) * 3 * c->M,
-                                                 cudaMemcpyDeviceToHost, s));
+                    // AoS copy into ring slot k on s, device-to-host copy on the copy
+                    // stream, overlapped with the next steps; slot k is rewritten only
+                    // after its previous copy has finished
+                    const int k = i % kOutSlots;
+                    double* slot = c->outbuf + (long long)k * step;
+                    MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->out_done[k], 0));
+                    mot::write_aos(c, n, slot, s);
+                    MOT_CUDA_TRY(cudaEventRecord(c->out_ready[k], s));
+                    MOT_CUDA_TRY(cudaStreamWaitEvent(c->cstream, c->out_ready[k], 0));
+                    MOT_CUDA_TRY(cudaMemcpyAsync(dst, slot, sizeof(double) * step,
+                                                 cudaMemcpyDeviceToHost, c->cstream));
+                    MOT_CUDA_TRY(cudaEventRecord(c->out_done[k], c->cstream));
                 }
                 c->stats.launches += 1;
             }
@@ -476,6 +559,7 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
                                      cudaMemcpyDeviceToHost, s));
         MOT_CUDA_TRY(cudaMemcpyAsync(hs, c->dstatus, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
         MOT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (J_out && !dev_out) MOT_CUDA_TRY(cudaStreamSynchronize(c->cstream));
         const int n0 = c->n_done;
         c->n_done += n_steps;
         c->last_iters = hs[0];

@@ -171,6 +171,169 @@ __global__ void __launch_bounds__(NT) k_inv_x(const typename CT<R>::c* __restric
     }
 }
 
+// ------------------------------------------------------------------ pass x, four-step codelets
+// For P = P1 P2 (64 = 8 x 8, 96 = 8 x 12, 210 = 14 x 15): 32 row pairs per CTA, each
+// pair a complex line of P points in shared memory ([P][33], line fastest).  Phase A
+// (warp n1 < P1, lane = line): x[n1 + P1 n2] -> DFT of length P2 over n2 in registers
+// (compile-time radices and twiddles, dft_ct) -> times W_P^{n1 k2}; phase B (warp
+// k2 < P2): DFT of length P1 over n1 -> X[k2 + P2 k1].  Every phase first reads its
+// values into registers, then (after a barrier) writes them back into the same buffer.
+constexpr int kXL = 32;          // row pairs per CTA
+constexpr int kXLD = kXL + 1;    // padded line stride of the shared buffer
+
+template <typename C, int P1, int P2, int DIR>
+__device__ __forceinline__ void x_four_step(C* X, const C* stw, int nvalid) {
+    constexpr int P = P1 * P2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    C x[P2];
+    if (warp < P1) {
+        const int n1 = warp;
+        Unroll1<0, P2>::run([&](auto q) {
+            constexpr int n2 = decltype(q)::value;
+            const int idx = n1 + P1 * n2;
+            C v;
+            v.x = 0; v.y = 0;
+            if (idx < nvalid) v = X[idx * kXLD + lane];
+            x[n2] = v;
+        });
+        dft_ct<P2, DIR>(x);
+        Unroll1<0, P2>::run([&](auto q) {
+            constexpr int k2 = decltype(q)::value;
+            C w = stw[(n1 * k2) % P];
+            if (DIR > 0) w.y = -w.y;
+            x[k2] = cmul(x[k2], w);
+        });
+    }
+    __syncthreads();
+    if (warp < P1)
+        Unroll1<0, P2>::run([&](auto q) {
+            constexpr int k2 = decltype(q)::value;
+            X[(warp * P2 + k2) * kXLD + lane] = x[k2];
+        });
+    __syncthreads();
+    C y[P1];
+    if (warp < P2) {
+        Unroll1<0, P1>::run([&](auto q) {
+            constexpr int n1 = decltype(q)::value;
+            y[n1] = X[(n1 * P2 + warp) * kXLD + lane];
+        });
+        dft_ct<P1, DIR>(y);
+    }
+    __syncthreads();
+    if (warp < P2)
+        Unroll1<0, P1>::run([&](auto q) {
+            constexpr int k1 = decltype(q)::value;
+            X[(warp + P2 * k1) * kXLD + lane] = y[k1];
+        });
+    __syncthreads();
+}
+
+template <typename R, int P1, int P2>
+__global__ void k_fwd_x4s(const double* __restrict__ in, int U, int V, int W,
+                          typename CT<R>::c* __restrict__ out,
+                          const typename CT<R>::c* __restrict__ tw,
+                          const double* __restrict__ scale) {
+    typedef typename CT<R>::c C;
+    constexpr int P = P1 * P2, Hu = P / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* X = reinterpret_cast<C*>(smem_raw);          // [P][kXLD]
+    C* stw = X + P * kXLD;                          // [P]
+    const int VP = (V + 1) / 2;
+    const long long npairs = 3LL * W * VP;
+    const long long pair0 = (long long)blockIdx.x * kXL;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    // z = a + i b of the two rows of a pair; positions >= U are the zero padding
+    for (int it = threadIdx.x; it < kXL * U; it += blockDim.x) {
+        const int t = it / U, j = it % U;
+        const long long pr = pair0 + t;
+        double va = 0.0, vb = 0.0;
+        if (pr < npairs) {
+            const long long cw = pr / VP;
+            const int v = (int)(pr % VP) * 2;
+            const double* row = in + (cw * V + v) * (long long)U;
+            va = row[j];
+            if (v + 1 < V) vb = row[U + j];
+            if (scale) {   // per-voxel factor (the adjoint transforms chi * lambda)
+                const long long m0 = ((cw % W) * V + v) * (long long)U + j;
+                va *= scale[m0];
+                if (v + 1 < V) vb *= scale[m0 + U];
+            }
+        }
+        C z;
+        z.x = (R)va;
+        z.y = (R)vb;
+        X[j * kXLD + t] = z;
+    }
+    __syncthreads();
+    x_four_step<C, P1, P2, -1>(X, stw, U);
+    // split: A = (Z[k] + conj Z[P-k]) / 2, B = -i (Z[k] - conj Z[P-k]) / 2
+    for (int it = threadIdx.x; it < kXL * Hu; it += blockDim.x) {
+        const int t = it / Hu, k = it % Hu;
+        const long long pr = pair0 + t;
+        if (pr >= npairs) continue;
+        const long long cw = pr / VP;
+        const int v = (int)(pr % VP) * 2;
+        const C zk = X[k * kXLD + t];
+        const C zm = X[((P - k) % P) * kXLD + t];
+        C A, B;
+        A.x = (R)0.5 * (zk.x + zm.x);
+        A.y = (R)0.5 * (zk.y - zm.y);
+        B.x = (R)0.5 * (zk.y + zm.y);
+        B.y = (R)0.5 * (zm.x - zk.x);
+        out[(cw * V + v) * (long long)Hu + k] = A;
+        if (v + 1 < V) out[(cw * V + v + 1) * (long long)Hu + k] = B;
+    }
+}
+
+template <typename R, int P1, int P2>
+__global__ void k_inv_x4s(const typename CT<R>::c* __restrict__ in, int U, int V, int W,
+                          R* __restrict__ out, const typename CT<R>::c* __restrict__ tw) {
+    typedef typename CT<R>::c C;
+    constexpr int P = P1 * P2, Hu = P / 2 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* X = reinterpret_cast<C*>(smem_raw);
+    C* stw = X + P * kXLD;
+    const int VP = (V + 1) / 2;
+    const long long npairs = 3LL * W * VP;
+    const long long pair0 = (long long)blockIdx.x * kXL;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    // Z[k] = A[k] + i B[k] and Z[P-k] = conj A[k] + i conj B[k] from the two halves
+    for (int it = threadIdx.x; it < kXL * Hu; it += blockDim.x) {
+        const int t = it / Hu, k = it % Hu;
+        const long long pr = pair0 + t;
+        C A, B;
+        A.x = 0; A.y = 0; B.x = 0; B.y = 0;
+        if (pr < npairs) {
+            const long long cw = pr / VP;
+            const int v = (int)(pr % VP) * 2;
+            A = in[(cw * V + v) * (long long)Hu + k];
+            if (v + 1 < V) B = in[(cw * V + v + 1) * (long long)Hu + k];
+        }
+        C z;
+        z.x = A.x - B.y;
+        z.y = A.y + B.x;
+        X[k * kXLD + t] = z;
+        if (k >= 1 && k < P - k) {
+            C zm;
+            zm.x = A.x + B.y;
+            zm.y = B.x - A.y;
+            X[(P - k) * kXLD + t] = zm;
+        }
+    }
+    __syncthreads();
+    x_four_step<C, P1, P2, +1>(X, stw, P);
+    for (int it = threadIdx.x; it < kXL * U; it += blockDim.x) {
+        const int t = it / U, j = it % U;
+        const long long pr = pair0 + t;
+        if (pr >= npairs) continue;
+        const long long cw = pr / VP;
+        const int v = (int)(pr % VP) * 2;
+        const C z = X[j * kXLD + t];
+        out[(cw * V + v) * (long long)U + j] = z.x;
+        if (v + 1 < V) out[(cw * V + v + 1) * (long long)U + j] = z.y;
+    }
+}
+
 // ------------------------------------------------------------------ strided passes
 struct MidArgs {
     int n_in, n_out;          // inputs read / outputs stored along the axis
@@ -385,6 +548,39 @@ void fft_free_axis(AxisFFT& a) {
     a.tw32 = nullptr;
 }
 
+// x passes through the four-step codelets where P has one (false: use the generic kernel)
+template <typename R, int P1, int P2>
+void launch_x4s(bool fwd, mot_ctx* c, const double* Jsoa, typename CT<R>::c* spec, R* real,
+                const double* scale, cudaStream_t s) {
+    typedef typename CT<R>::c C;
+    constexpr int P = P1 * P2;
+    const size_t sm = sizeof(C) * ((size_t)P * kXLD + P);
+    const int threads = 32 * (P1 > P2 ? P1 : P2);
+    const long long npairs = 3LL * c->W * ((c->V + 1) / 2);
+    const int blocks = (int)((npairs + kXL - 1) / kXL);
+    if (fwd) {
+        set_smem(k_fwd_x4s<R, P1, P2>, sm);
+        k_fwd_x4s<R, P1, P2><<<blocks, threads, sm, s>>>(Jsoa, c->U, c->V, c->W, spec,
+                                                         table<R>(c->ax[0]), scale);
+    } else {
+        set_smem(k_inv_x4s<R, P1, P2>, sm);
+        k_inv_x4s<R, P1, P2><<<blocks, threads, sm, s>>>(spec, c->U, c->V, c->W, real,
+                                                         table<R>(c->ax[0]));
+    }
+    MOT_LAUNCH_CHECK();
+}
+
+template <typename R>
+bool x_pass_codelet(bool fwd, mot_ctx* c, const double* Jsoa, typename CT<R>::c* spec, R* real,
+                    const double* scale, cudaStream_t s) {
+    switch (c->ax[0].P) {
+        case 64: launch_x4s<R, 8, 8>(fwd, c, Jsoa, spec, real, scale, s); return true;
+        case 96: launch_x4s<R, 8, 12>(fwd, c, Jsoa, spec, real, scale, s); return true;
+        case 210: launch_x4s<R, 14, 15>(fwd, c, Jsoa, spec, real, scale, s); return true;
+        default: return false;
+    }
+}
+
 template <typename R>
 void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStream_t s,
                  const double* scale) {
@@ -394,7 +590,7 @@ void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStr
     const int U = c->U, V = c->V, W = c->W;
     const int Pu = c->ax[0].P, Pv = c->ax[1].P, Pw = c->ax[2].P, Hu = c->Hu;
     // x
-    {
+    if (!x_pass_codelet<R>(true, c, Jsoa, hb.tmp1, nullptr, scale, s)) {
         const long long npairs = 3LL * W * ((V + 1) / 2);
         const size_t sm = smem_bytes<R>(Pu);
         set_smem(k_fwd_x<R>, sm);
@@ -448,7 +644,7 @@ void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s
         mid_pass<R>(hb.tmp2, hb.tmp1, c->ax[1], a, s);
     }
     // x: c2r
-    {
+    if (!x_pass_codelet<R>(false, c, nullptr, hb.tmp1, out, nullptr, s)) {
         const long long npairs = 3LL * W * ((V + 1) / 2);
         const size_t sm = smem_bytes<R>(Pu);
         set_smem(k_inv_x<R>, sm);

@@ -114,7 +114,17 @@ struct mot_ctx {
     int* dstatus = nullptr;      // [0] cg iterations of last step, [1] flags
     double* norms = nullptr;     // per-step ||J_n||^2 of the current call
     int norms_cap = 0;
-    double* outbuf = nullptr;    // one step of AoS J for host outputs
+    double* outbuf = nullptr;    // kOutSlots steps of AoS J for host outputs (a ring)
+    // host transfers overlapped with the march: copy streams (device-to-host outputs,
+    // host-to-device excitation, so both directions run at once), per-slot events of the
+    // output ring (AoS J written / copied out), and per-chunk events of a host
+    // excitation being staged
+    cudaStream_t cstream = nullptr;
+    cudaStream_t hstream = nullptr;
+    cudaEvent_t out_ready[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t out_done[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> e_chunk;
+    int e_chunk_steps = 0;       // steps per staged chunk; 0: staged synchronously on the stream
     double last_norm = 0.0;
     double peak_norm = 0.0;
     int fail_step = 0;
@@ -128,6 +138,7 @@ struct mot_ctx {
 
     // excitation staging
     double* Estage = nullptr;    // [cap][M][3]
+    double* pw_tab = nullptr;    // [kPwTable] plane-wave voxel-average table (excitation.cu)
     int E_cap = 0, E_count = 0, E_first = 0;  // steps staged, first staged n
 
     HistoryBuffers<double> h64;
@@ -176,6 +187,7 @@ template <> inline HistoryBuffers<float>& hbuf<float>(mot_ctx* c) { return c->h3
 namespace mot {
 
 constexpr int WIN = 8;  // lag window per octant offset of the interaction table
+constexpr int kPwTable = 1 << 16;   // nodes of the plane-wave table of one call
 
 // quadrature.cu
 void compute_table(mot_ctx* c);

@@ -421,5 +421,5 @@ class Context:
 
     def set_solver(self, tol=None, max_iter=200, growth_limit=1e12):
         if tol is None:
-            tol = 1e-13 if self._precision == "fp64" else 1e-10
+            tol = 1e-13 if self._precision == "fp64" else 3e-8
         self._check(self._lib.mot_set_solver(self._h, tol, max_iter, growth_limit))

@@ -91,6 +91,26 @@ def test_excitation_matches_oracle(mot):
     assert np.abs(E - ref).max() < 1e-13 * np.abs(ref).max()
 
 
+def test_excitation_long_call_oblique(mot):
+    """One call of 12,000 steps (several tables of the interpolated voxel average) with an
+    oblique wave and a short pulse, sampled at its start, middle and end against the
+    oracle's tensor rule."""
+    from oracle import excitation
+    eps = wl.cube(10, 6.0)
+    p = {"k_hat": np.array([0.48, -0.6, 0.64]), "p_hat": np.array([0.8, 0.6, 0.0]),
+         "f_c": 0.11, "sigma_t": 5.0}
+    n = 12000
+    with mot.Context(eps) as ctx:
+        for t0 in (40.0, 6050.0, 11990.0):
+            q = dict(p, t0=t0)
+            E = ctx.plane_wave(q["k_hat"], q["p_hat"], q["f_c"], q["sigma_t"], t0, 1, n)
+            for a in (0, 6000, n - 30):
+                ref = excitation.tested_excitation(eps, q, 30, n_first=a + 1)
+                scale = max(np.abs(ref).max(), 1e-300)
+                if scale > 1e-12:
+                    assert np.abs(E[a:a + 30] - ref).max() < 1e-13 * scale, (t0, a)
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32_history"])
 def test_history_matches_direct_sum(mot, cube8_oracle, precision):
     """P_{n-1} = sum_l Z_l J_{n-l} through the FFT / ring / MAC path equals the
