@@ -52,30 +52,53 @@ __device__ __forceinline__ long long jslot(int s0, int l, int jring, long long s
 // per-voxel factors precomputed at setup (no FP64 divisions in the step):
 //   f[0][m] = T(1)/eps_m = 0.5/eps_m, f[1][m] = 1/chi_m (0 if chi_m = 0),
 //   f[2][m] = 1/(T(0)/eps_m + delta_0) (used where chi_m = 0), f[3][m] = chi_m
+// One thread per voxel, its three components: the AoS excitation row and the four
+// factors are read once and coalesced (a thread per component would read E with a
+// stride of three and every factor three times).  All loads come before the stores
+// (the new slot Jn lies in the same ring the loads read from, so loads placed after a
+// store could not be moved ahead of it), and the FIR terms of lags 1..3 reuse them.
 template <typename R>
 __global__ void k_epilogue(long long M, const double* __restrict__ f, const double* __restrict__ En,
                            const R* __restrict__ hist, double* __restrict__ Jring, int s0,
                            int jring, Taps tp, double* __restrict__ b) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 3 * M) return;
-    const long long m = i % M;
-    const int beta = (int)(i / M);
+    const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
     const long long st = 3 * M;
-    const double e = En ? En[m * 3 + beta] : 0.0;
-    const double j1 = Jring[jslot(s0, 1, jring, st) + i];
-    const double j2 = Jring[jslot(s0, 2, jring, st) + i];
-    const double j3 = Jring[jslot(s0, 3, jring, st) + i];
-    double P = f[m] * j1 - f[3 * M + m] * (double)hist[i];
-    for (int l = 1; l < tp.n; ++l) P += tp.d[l] * Jring[jslot(s0, l, jring, st) + i];
-    const double rhs = e - P;
+    const double f0 = f[m], ichi = f[M + m], f2 = f[2 * M + m], chi = f[3 * M + m];
+    const double* r1 = Jring + jslot(s0, 1, jring, st);
+    const double* r2 = Jring + jslot(s0, 2, jring, st);
+    const double* r3 = Jring + jslot(s0, 3, jring, st);
     double* Jn = Jring + jslot(s0, 0, jring, st);
-    const double ichi = f[M + m];
-    if (ichi > 0.0) {
-        b[i] = rhs * ichi;
-        Jn[i] = 3.0 * j1 - 3.0 * j2 + j3;      // quadratic extrapolation as CG start
-    } else {
-        b[i] = 0.0;
-        Jn[i] = rhs * f[2 * M + m];
+    double e[3], j1[3], j2[3], j3[3], P[3];
+#pragma unroll
+    for (int beta = 0; beta < 3; ++beta) {
+        const long long i = beta * M + m;
+        e[beta] = En ? En[m * 3 + beta] : 0.0;
+        j1[beta] = r1[i];
+        j2[beta] = r2[i];
+        j3[beta] = r3[i];
+        P[beta] = f0 * j1[beta] - chi * (double)hist[i];
+    }
+#pragma unroll
+    for (int beta = 0; beta < 3; ++beta) {
+        const long long i = beta * M + m;
+        for (int l = 1; l < tp.n; ++l) {
+            const double jl = l == 1 ? j1[beta] : l == 2 ? j2[beta] : l == 3 ? j3[beta]
+                                                  : Jring[jslot(s0, l, jring, st) + i];
+            P[beta] += tp.d[l] * jl;
+        }
+    }
+#pragma unroll
+    for (int beta = 0; beta < 3; ++beta) {
+        const long long i = beta * M + m;
+        const double rhs = e[beta] - P[beta];
+        if (ichi > 0.0) {
+            b[i] = rhs * ichi;
+            Jn[i] = 3.0 * j1[beta] - 3.0 * j2[beta] + j3[beta];   // quadratic extrapolation as CG start
+        } else {
+            b[i] = 0.0;
+            Jn[i] = rhs * f2;
+        }
     }
 }
 
@@ -1021,7 +1044,7 @@ void chebyshev_setup(mot_ctx* c) {
 
 template <typename R>
 void epilogue(mot_ctx* c, int n, const double* En, cudaStream_t s) {
-    const long long tot = 3 * c->M;
+    const long long tot = c->M;
     k_epilogue<R><<<(int)((tot + NT - 1) / NT), NT, 0, s>>>(
         c->M, c->vfac, En, hbuf<R>(c).hist_spatial, c->J, (int)slot_index(n, c->jring), c->jring,
         taps_of(c), c->rhs);

@@ -73,3 +73,25 @@ def test_fir_magnitude_host_call(lib):
     for k, name in ((1, "fir2"), (2, "fir3"), (3, "fir4")):
         mag = mot.fir_magnitude(wl.fir_taps(name, 0.1), th)
         assert np.abs(mag - 0.1 * np.sin(th / 2) ** k).max() < 1e-15
+
+
+def test_diagnostic_entry_points_reject_bad_arguments_on_the_host(lib):
+    """The PDSA, truncation and frequency-response entry points validate their
+    arguments before any device work (NULL context, bad sizes) and return MOT_ERR_ARG."""
+    import numpy as np
+    out = np.zeros(8)
+    info = (ctypes.c_int * 2)()
+    assert lib.mot_pdsa_apply(None, 0, 0, out.ctypes.data, out.ctypes.data) == 1
+    assert lib.mot_pdsa_bounds(None, 0, 0, out.ctypes.data) == 1
+    assert lib.mot_pdsa_lanczos(None, 0, 0, 4, 1, 1, out.ctypes.data,
+                                ctypes.cast(info, ctypes.c_void_p), out.ctypes.data) == 1
+    assert lib.mot_truncate_table(None, 1e-6) == 1
+    J = np.zeros((4, 1, 3))
+    f = np.array([0.1])
+    e_bad = np.array([1.0])                      # eps_r must exceed 1 at a probe
+    assert lib.mot_frequency_response(4, 1, J.ctypes.data, 1.0, 0.2, e_bad.ctypes.data, 0.1,
+                                      5.0, 1, f.ctypes.data, out.ctypes.data, None) == 1
+    e_ok = np.array([4.0])
+    assert lib.mot_frequency_response(4, 1, J.ctypes.data, 1.0, 1.5, e_ok.ctypes.data, 0.1,
+                                      5.0, 1, f.ctypes.data, out.ctypes.data, None) == 1
+    assert lib.mot_fir_magnitude(None, 3, 1, f.ctypes.data, out.ctypes.data) == 1
