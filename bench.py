@@ -202,6 +202,32 @@ def job_throughput(units_per_rank, seconds, world):
 
 # ------------------------------------------------------------------ our arm
 
+def cufft_comparison(P, U, V, W, dtype_name):
+    """Time of one library FFT (cuFFT through torch.fft.rfftn) of the same zero-padded
+    three-component grid that the forward FFT phase transforms, for comparison only: it
+    transforms the full padded cube (no pruning of the zero padding).  Returns ms per
+    transform, or None if it cannot run."""
+    try:
+        import torch
+        dt = torch.float32 if dtype_name == "fp32_history" else torch.float64
+        x = torch.zeros((3, P[2], P[1], P[0]), dtype=dt, device="cuda")
+        x[:, :W, :V, :U] = torch.rand((3, W, V, U), dtype=dt, device="cuda")
+        for _ in range(3):
+            torch.fft.rfftn(x, dim=(1, 2, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n = 20
+        e0.record()
+        for _ in range(n):
+            torch.fft.rfftn(x, dim=(1, 2, 3))
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+    except Exception:
+        return None
+
+
 def march_timed(ctx, torch, stream, E, n_steps, dev, world):
     """Time n_steps of mot_march (excitation staged from the device tensor E)."""
     ctx.set_excitation(E, stream=stream)
@@ -282,6 +308,11 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
                      "algorithmic_bytes_per_launch": b_launch},
         "clocks": clocks, "ell": info["ell"], "P": list(info["P"]), "levels": ctx.levels,
     }
+    W_, V_, U_ = eps.shape
+    out["fft_comparison"] = {
+        "ours_forward_fft_ms": st["ms_fft_fwd"] / max(st["steps"], 1),
+        "cufft_rfftn_full_padded_ms": cufft_comparison(info["P"], U_, V_, W_, prec),
+        "note": "timing comparison only; cuFFT transforms the full padded grid"}
     e2e = None
     if want_e2e:
         k = per                                  # one bench step through host buffers

@@ -128,13 +128,13 @@ def pdsa_scan(sides, eps_r=12.0, k=20000, fp32_spectrum=False, all_n=False, k_n=
                    "bracket": [b["lo"], b["hi"]], "chi_max": b["chi_max"],
                    "fp32_spectrum": fp32_spectrum}
             if r["theta_min"] < -r["resid_min"]:
-                row["verdict"] = "indefinite (negative Ritz value)"
+                row["status"] = "indefinite (negative Ritz value)"
             elif b["lo"] > 0.0:
-                row["verdict"] = "positive definite (bracket)"
+                row["status"] = "positive definite (bracket)"
             elif r["resid_min"] < 0.01 * r["theta_min"]:
-                row["verdict"] = "converged smallest Ritz value > 0"
+                row["status"] = "converged smallest Ritz value > 0"
             else:
-                row["verdict"] = "not converged in %d steps" % r["steps"]
+                row["status"] = "not converged in %d steps" % r["steps"]
             # delta that lifts the estimate theta_min - resid_min of lambda_min to 0
             row["delta_guided"] = max(0.0, -(r["theta_min"] - r["resid_min"])) * b["chi_max"]
             row["delta_paper"] = 1e-7 * N ** 3
