@@ -17,6 +17,12 @@ The headline value is the first variant (FP32-history, blocked).  Inputs (the
 excitation of every timed time step) are resident in HBM before the timed region; the
 spectral ring (tens of GB) is far larger than L2, so no flush is needed.
 
+Besides the contract's keys, each variant reports its phase times (CUDA events on the
+march stream), the roofline of its dominant history kernel, and a timing-only
+comparison of its forward FFT phase with cuFFT (torch.fft.rfftn) on the full padded
+grid.  `e2e` marches one bench step from pinned host excitation to pinned host J
+through the library's overlapped transfers.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 import argparse
