@@ -99,6 +99,28 @@ def test_z0_symmetrised_is_spd():
     assert np.linalg.eigvalsh(A).min() > 0.0
 
 
+def test_reciprocity_of_every_lag():
+    """Reciprocity (Sec. 6: the matrices are symmetric): diag(1/chi) Z_l is symmetric
+    for every lag l on a heterogeneous grid with a vacuum voxel excluded, and the
+    unscaled Z_l is not (the chi factor multiplies rows), so a column-scaled assembly
+    fails this test."""
+    N = 3
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, ell + 1)
+    rng = np.random.default_rng(9)
+    eps_r = 2.0 + 9.0 * rng.uniform(size=(N, N, N))
+    e = np.repeat(eps_r.reshape(-1), 3)
+    chi = (e - 1) / e
+    taps = wl.fir_taps("fir3", 0.05)
+    for l in range(ell + 1):
+        Z = march.dense_Z(G, l, eps_r, taps)
+        A = Z / chi[:, None]
+        scale = np.abs(A).max()
+        assert np.abs(A - A.T).max() <= 1e-15 * scale, l
+        if np.abs(Z - np.diag(np.diag(Z))).max() > 1e-6 * scale:
+            assert np.abs(Z - Z.T).max() > 1e-8 * scale, l
+
+
 def test_pdsa_binomials_and_fir_identity():
     """D_0 = Z_0, D_ell = sum (-1)^i Z_i, and FIR taps with sum (-1)^n delta_n = delta
     shift D_ell by exactly delta I (Eqs. Dn, Regularization, RegReq1)."""
