@@ -113,6 +113,12 @@ void mot_destroy(mot_ctx* ctx);
  *            buffer, which is reallocated if n_steps exceeds its capacity
  *  stream    cudaStream_t to use, or NULL for the context's stream
  * Steps without staged excitation are marched with E = 0.
+ * A host E is copied in ~64 MB chunks on a staging stream of the context, and
+ * mot_march waits only for the chunk of the step it is about to solve, so the copy
+ * overlaps the march.  Pageable host memory is captured before this call returns;
+ * page-locked (pinned) host memory is read while the copy runs, so keep it unchanged
+ * until mot_march has returned from the steps that consume it.
+ * A device E is copied on `stream`, ordered like the caller's own work there.
  */
 mot_status mot_set_excitation(mot_ctx* ctx, int n_steps, const double* E, void* stream);
 
@@ -156,7 +162,10 @@ mot_status mot_plane_wave_static(mot_ctx* ctx, const double k_hat[3], const doub
 /*
  * mot_march - advance the march by n_steps time steps.
  *  J_out     [n_steps][M][3] doubles receiving J_{n0+1} .. J_{n0+n_steps} (host or
- *            device pointer), or NULL to keep the result on the device only
+ *            device pointer), or NULL to keep the result on the device only; a host
+ *            J_out is filled through a 3-slot device ring whose device-to-host copies
+ *            run on a copy stream while the next steps compute, and is complete when
+ *            the call returns
  *  stream    cudaStream_t or NULL
  * Errors: MOT_ERR_NOT_CONVERGED (CG exceeded max_iter; J of that step is the last
  * iterate), MOT_ERR_UNSTABLE (NaN/Inf or ||J_n|| above the growth limit; see
