@@ -43,6 +43,7 @@ import workloads as wl  # noqa: E402
 
 CONFIG_NAME = "sphere104"
 REF_SAMPLE_N = 10          # oracle sample grid (its direct sum is O(M^2) per step)
+REF_STEPS_PER_BENCH_STEP = 24   # oracle time steps per bench step (~3 s of CPU work)
 
 
 def parse():
@@ -434,7 +435,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        ref = oracle_sample(max(args.steps, 8), args.warmup)
+        ref = oracle_sample(REF_STEPS_PER_BENCH_STEP * max(args.steps, 1), args.warmup)
         line = {"impl": "reference", "metric": "voxel-timesteps/s", "value": ref["value"],
                 "unit": "voxel-timesteps/s", "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
@@ -453,7 +454,7 @@ def main():
     head = results[head_key]
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(24, 2)
+        cpu = oracle_sample(4 * REF_STEPS_PER_BENCH_STEP, 2)   # ~10 s of CPU work
     if rank != 0:
         return
     M = wl.config(args.config)["eps_r"].size
