@@ -100,12 +100,10 @@ __global__ void interleave_kernel(const double* __restrict__ src, long long noct
     dst[i] = (R)src[cc * noct + o];
 }
 
-template <typename R>
-__global__ void store_kernel(const double* __restrict__ src, long long n, double scale,
-                             R* __restrict__ dst) {
+// x[i] *= s (in place)
+__global__ void scale_inplace_kernel(double* x, long long n, double s) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    dst[i] = (R)(src[i] * scale);
+    if (i < n) x[i] *= s;
 }
 
 inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
@@ -147,7 +145,7 @@ void transform_one(mot_ctx* c, const TrigTables& tt, Scratch& sc, int cc, double
     pass_mid<<<nblk((long long)Hw * Hv * Hu, 256), 256, 0, s>>>(sc.t2, W, Hv * Hu, 1, wz, Hw, dst);
     MOT_LAUNCH_CHECK();
     if (odd) {   // two odd axes: (-i)(-i) = -1
-        store_kernel<double><<<nblk(c->noct, 256), 256, 0, s>>>(dst, c->noct, -1.0, dst);
+        scale_inplace_kernel<<<nblk(c->noct, 256), 256, 0, s>>>(dst, c->noct, -1.0);
         MOT_LAUNCH_CHECK();
     }
 }
