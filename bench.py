@@ -27,7 +27,6 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 """
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
