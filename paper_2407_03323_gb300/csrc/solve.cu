@@ -1020,7 +1020,9 @@ void chebyshev_setup(mot_ctx* c) {
     const int k = (int)al.size();
     const double tmin = tridiag_eig(al, be, 0, lo, hi);
     const double tmax = tridiag_eig(al, be, k - 1, lo, hi);
-    if (!(tmin > 0.0) || !(tmax > tmin))
+    // tmax == tmin when A is a multiple of the identity (a single voxel: G_0(0) is
+    // isotropic); the interval [tmin, 1.02 tmax] below is still non-empty
+    if (!(tmin > 0.0) || !(tmax >= tmin))
         throw MotError{MOT_ERR_ARG, "diag(1/chi) Z_0 is not positive definite on this grid"};
     const double A = tmin, B = 1.02 * tmax;
     c->cheb_lmin = A;
