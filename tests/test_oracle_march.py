@@ -338,3 +338,21 @@ def test_response_pins():
     sel = (fr >= 0) & (fr < 0.1)
     ref = response.incident_amplitude(fr[sel], fc, st)
     assert np.abs(X[sel] - ref).max() < 1e-10 * ref.max()
+
+
+def test_pdsa_smallest_eigenvalue_is_at_n_ell_and_falls_with_N():
+    """PDSA on eps_r = 12 cubes (Sec. 5.1): over n = 0..ell the smallest eigenvalue of
+    A_n = diag(1/chi) D_n / C(ell, n) is the one of D_ell, and lambda_min(A_ell) is
+    positive and falls as the cube grows (N = 3, 4, 6), the trend behind the paper's
+    loss of definiteness at larger N."""
+    mins = []
+    for N in (3, 4, 6):
+        ell = num_lags(N, N, N)
+        G, _, _ = kernel_table.octant_table(N, ell + 1)
+        eps = wl.cube(N, 12.0)
+        lam = [np.linalg.eigvalsh(pdsa.scaled_pdsa_matrix(G, eps, np.zeros(0), ell, n)).min()
+               for n in (range(ell + 1) if N < 6 else (0, ell // 2, ell - 1, ell))]
+        assert int(np.argmin(lam)) == len(lam) - 1
+        assert lam[-1] > 0.0
+        mins.append(lam[-1])
+    assert mins[0] > mins[1] > mins[2]
