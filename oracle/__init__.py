@@ -21,6 +21,8 @@ Contents (each function cites the passage of the paper it follows):
                     FFT of the embedded kernel, 3x3 eigenvalues per bin)
 * ``response``      tapered frequency response |H^alpha| (Eq. Halpha) and the incident
                     pulse's amplitude spectrum
+* ``probes``        scattered field at probe voxels outside the grid (objective of the
+                    adjoint workload) and its transposed operator (the adjoint source)
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against closed
 forms, sum rules, exact identities or brute force, except the absolute physical

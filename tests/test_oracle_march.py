@@ -356,3 +356,53 @@ def test_pdsa_smallest_eigenvalue_is_at_n_ell_and_falls_with_N():
         assert lam[-1] > 0.0
         mins.append(lam[-1])
     assert mins[0] > mins[1] > mins[2]
+
+
+def test_probe_field_pins():
+    """Probe field of the adjoint workload's objective (reading R18): probes placed on
+    voxels of the grid itself reproduce the dense history rows sum_l dense_G(l) J_{n-l}
+    (an independent assembly from the octant table); Fibonacci probes sit at the
+    requested distance, outside the grid."""
+    from oracle import probes as pr
+    N = 3
+    ell = num_lags(N, N, N)
+    G, _, _ = kernel_table.octant_table(N, ell + 1)
+    rng = np.random.default_rng(17)
+    J = rng.normal(size=(6, N ** 3, 3))
+    inside = np.array([(0, 0, 0), (2, 1, 0), (1, 2, 2)])
+    Gp = pr.probe_elements(inside, (N, N, N), ell + 1)
+    E = pr.probe_field(Gp, J)
+    dense = [march.dense_G(G, l, N, N, N) for l in range(ell + 1)]
+    for n in range(J.shape[0]):
+        ref = sum(dense[l] @ J[n - l].reshape(-1) for l in range(min(ell + 1, n + 1)))
+        for k, (u, v, w) in enumerate(inside):
+            m = u + N * (v + N * w)
+            assert np.abs(E[n, k] - ref[3 * m:3 * m + 3]).max() <= 1e-14 * np.abs(ref).max()
+    P = pr.fibonacci_probes(8, 64)
+    c = P + 0.5 - 4.0
+    r = np.linalg.norm(c, axis=1)
+    assert len(P) >= 60 and np.all(np.abs(r - 16.0) <= 0.87)
+    assert np.all(((P < 0) | (P > 7)).any(axis=1))    # every probe outside the 8^3 grid
+
+
+def test_probe_objective_gradient_against_differences():
+    """The transposed probe operator gives dO/dJ of the gated probe energy: central
+    differences in a few entries of J (O is quadratic in J, so they are exact up to
+    rounding)."""
+    from oracle import probes as pr
+    N = 2
+    nlag = 12
+    P = np.array([(5, 1, 0), (-3, 0, 2), (1, 6, -2)])
+    Gp = pr.probe_elements(P, (N, N, N), nlag)
+    rng = np.random.default_rng(23)
+    J = rng.normal(size=(10, N ** 3, 3))
+    first = 4
+    E = pr.probe_field(Gp, J)
+    g = pr.probe_objective_gradient(Gp, E, first)
+    h = 1e-3
+    for (k, m, b) in [(0, 0, 0), (3, 5, 2), (7, 2, 1), (9, 7, 0)]:
+        Jp = J.copy(); Jp[k, m, b] += h
+        Jm = J.copy(); Jm[k, m, b] -= h
+        fd = (pr.probe_objective(pr.probe_field(Gp, Jp), first)
+              - pr.probe_objective(pr.probe_field(Gp, Jm), first)) / (2 * h)
+        assert abs(fd - g[k, m, b]) <= 1e-8 * max(1.0, abs(g).max()), (k, m, b, fd, g[k, m, b])
