@@ -221,6 +221,8 @@ class Context:
         return c
 
     def close(self):
+        """Destroy the context (mot_destroy); refused while contexts shared from it
+        are alive."""
         if getattr(self, "_h", None):
             live = [r() for r in getattr(self, "_shares", [])]
             if any(c is not None and getattr(c, "_h", None) for c in live):
@@ -242,12 +244,16 @@ class Context:
 
     # -- API
     def set_excitation(self, E, stream=None):
+        """Stage E[n][M][3] (float64, numpy or CUDA tensor) for the next steps
+        (mot_set_excitation); steps without staged excitation march with E = 0."""
         if not _dtype_ok(E):
             raise TypeError("E must be float64")
         n = E.shape[0]
         self._check(self._lib.mot_set_excitation(self._h, n, _ptr(E), _stream(stream)))
 
     def plane_wave(self, k_hat, p_hat, f_c, sigma_t, t0, n_first, n_steps, out=None, stream=None):
+        """Tested modulated-Gaussian plane wave E[n_steps][M][3] of steps n_first..
+        (mot_plane_wave, Eq. E); out: numpy array or CUDA tensor, else a new array."""
         if out is None:
             out = np.zeros((n_steps, self.M, 3))
         k = np.ascontiguousarray(k_hat, dtype=np.float64)
@@ -324,6 +330,8 @@ class Context:
         self._check(self._lib.mot_restart(self._h, n0, k, _ptr(J_hist), _stream(stream)))
 
     def eval_history(self, J_hist, out=None, stream=None):
+        """P_{n-1} = sum_l Z_l J_{n-l} for a given past J_hist[l-1] = J_{n-l}
+        (mot_eval_history), through the same FFT / ring / MAC path as the march."""
         J = J_hist
         if isinstance(J, np.ndarray):
             J = np.ascontiguousarray(J, dtype=np.float64)
@@ -334,12 +342,16 @@ class Context:
         return out
 
     def table(self, l0, n_lags):
+        """Elements G_l^{ab}(d) of lags l0.. on the octant of offsets
+        (mot_get_table): [n_lags][6][W][V][U], components xx yy zz xy xz yz."""
         W, V, U = self.shape
         out = np.zeros((n_lags, 6, W, V, U))
         self._check(self._lib.mot_get_table(self._h, l0, n_lags, out.ctypes.data))
         return out
 
     def spectrum(self, l):
+        """Octant spectrum of lag l (mot_get_spectrum): [6][Pw/2+1][Pv/2+1][Pu/2+1],
+        unnormalised."""
         Pu, Pv, Pw = self.P
         out = np.zeros((6, Pw // 2 + 1, Pv // 2 + 1, Pu // 2 + 1))
         self._check(self._lib.mot_get_spectrum(self._h, l, out.ctypes.data))
@@ -398,6 +410,8 @@ class Context:
         return out
 
     def info(self):
+        """ell, padded sizes P, steps done, last ||J||, first failing step and the
+        last CG iteration count (mot_get_info)."""
         ell = ctypes.c_int()
         P = (ctypes.c_int * 3)()
         nd = ctypes.c_int()
@@ -412,14 +426,18 @@ class Context:
                 "fail_step": fs.value, "last_cg_iters": it.value}
 
     def set_profiling(self, enable=True):
+        """Per-phase event timing in march and counter reset (mot_set_profiling)."""
         self._check(self._lib.mot_set_profiling(self._h, 1 if enable else 0))
 
     def stats(self):
+        """Launch, step and CG counters and the per-phase times (mot_get_stats)."""
         st = Stats()
         self._check(self._lib.mot_get_stats(self._h, ctypes.byref(st)))
         return {k: getattr(st, k) for k, _ in Stats._fields_}
 
     def set_solver(self, tol=None, max_iter=200, growth_limit=1e12):
+        """Z_0 solve tolerance (default 1e-13 FP64, 3e-8 FP32-history), inner
+        iteration cap and the growth limit of the stability monitor (mot_set_solver)."""
         if tol is None:
             tol = 1e-13 if self._precision == "fp64" else 3e-8
         self._check(self._lib.mot_set_solver(self._h, tol, max_iter, growth_limit))
