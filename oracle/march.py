@@ -119,3 +119,44 @@ def residual(Goct, eps_r, taps, E, J):
             acc = acc + Zs[l] @ Jf[n - l]
         worst = max(worst, float(np.abs(acc).max()))
     return worst / max(float(np.abs(E).max()), 1e-300)
+
+
+def history_sparse(eps_r, taps, src, Jsrc, tgt, nlag, elements=None):
+    """P_{n-1} = sum_{l=1}^{nlag-1} Z_l J_{n-l} (Eq. PnMOT, FIR taps included) at the
+    voxels `tgt` for a history supported on the voxels `src` only:
+    Jsrc[l-1][k] = J_{n-l} at voxel src[k] (shape (nlag-1, len(src), 3)).  Each element
+    block G_l(d) comes from ``kernel_table.offset_elements`` at |d| with the parity signs,
+    so no octant table of the whole grid is needed.  `elements` may hold a dict
+    |d| -> (vol, face) to reuse between calls.  Returns (len(tgt), 3)."""
+    from .kernel_table import offset_elements
+    W, V, U = eps_r.shape
+    e = eps_r.reshape(-1)
+    chi = (e - 1.0) / e
+    idx = offsets_and_index(U, V, W)
+    cache = {} if elements is None else elements
+    nh = Jsrc.shape[0]
+    out = np.zeros((len(tgt), 3))
+    for i, m in enumerate(tgt):
+        acc = np.zeros(3)
+        for k, s in enumerate(src):
+            d = idx[m] - idx[s]
+            key = tuple(int(v) for v in np.abs(d))
+            if key not in cache:
+                cache[key] = offset_elements(key, nlag)
+            vol, face = cache[key]
+            sg = np.sign(d)
+            G = face.copy()                          # [a][b][l]
+            for a in range(3):
+                for b in range(3):
+                    if a != b:
+                        G[a, b] *= sg[a] * sg[b]
+                G[a, a] -= vol
+            for l in range(1, min(nh, nlag - 1) + 1):
+                acc -= chi[m] * (G[:, :, l] @ Jsrc[l - 1, k])
+        where = np.nonzero(np.asarray(src) == m)[0]
+        for k in where:                              # identity part at a source voxel
+            for l in range(1, min(nh, nlag - 1) + 1):
+                coef = T_at_lag(l) / e[m] + (taps[l] if l < len(taps) else 0.0)
+                acc += coef * Jsrc[l - 1, k]
+        out[i] = acc
+    return out
