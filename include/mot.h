@@ -149,6 +149,8 @@ mot_status mot_plane_wave(mot_ctx* ctx, const double k_hat[3], const double p_ha
  *             longer requests over several calls (n_first advances by n_steps)
  *  set-up     the first call on a device resolves the array's address there (and may
  *             load the module): make it before any stream capture on that device
+ *  device     runs on the device the context was created on, whichever device is
+ *             current; the caller's current device is restored before returning
  *  zeroing    none needed: every staged element is written before it is copied out
  *  races      one array per device per process: calls that overlap in time (several
  *             host threads, any contexts on the same device) overwrite each other's
@@ -416,6 +418,20 @@ mot_status mot_set_profiling(mot_ctx* ctx, int enable);
 
 /* Copy the counters (see mot_stats) to *out (host pointer). */
 mot_status mot_get_stats(const mot_ctx* ctx, mot_stats* out);
+
+/*
+ * mot_fma_peak - measure the current device's sustained FMA rate (no counterpart in the
+ * paper: the denominator of the roofline of kernels bound by arithmetic rather than
+ * memory, such as the FP64 history kernels on GPUs whose FP64 rate is a fraction of
+ * their FP32 rate).  One launch of independent FMA chains on every SM, timed with CUDA
+ * events on the default stream after a warm-up launch; synchronous.
+ *  fp64   1: double-precision FMAs, 0: single precision
+ *  iters  FMA iterations per chain (>= 1); choose it for a launch of ~0.1 s
+ *  ms     receives the launch's duration in milliseconds
+ *  flops  receives the floating-point operations it performed (2 per FMA)
+ * Errors: MOT_ERR_ARG (NULL outputs, iters < 1), MOT_ERR_OOM, MOT_ERR_CUDA.
+ */
+mot_status mot_fma_peak(int fp64, int iters, float* ms, double* flops);
 
 /* Last error message of ctx, or of the last failed mot_create when ctx is NULL. */
 const char* mot_last_error(const mot_ctx* ctx);

@@ -44,7 +44,7 @@ class MarchFunction(torch.autograd.Function):
         M = ctx.M
         K = checkpoint_every or n_steps
         seg = min(K, n_steps)
-        probe_idx = None if probes is None else torch.as_tensor(probes, device="cuda")
+        probe_idx = None if probes is None else torch.as_tensor(probes, device="cuda").long()
         out_cols = M if probe_idx is None else probe_idx.numel()
         J_out = torch.empty((n_steps, out_cols, 3), dtype=torch.float64, device="cuda")
         keep_all = checkpoint_every is None
@@ -83,7 +83,8 @@ class MarchFunction(torch.autograd.Function):
             if fctx.probe_idx is None:
                 return grad_out[lo - 1:hi].contiguous()
             g = torch.zeros((hi - lo + 1, M, 3), dtype=torch.float64, device="cuda")
-            g[:, fctx.probe_idx] = grad_out[lo - 1:hi]
+            # a voxel listed twice among the probes receives both contributions
+            g.index_add_(1, fctx.probe_idx, grad_out[lo - 1:hi])
             return g
 
         adj = Context(fctx.eps, fctx.taps, **fctx.options)

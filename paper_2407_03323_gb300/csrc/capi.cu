@@ -202,7 +202,9 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
     mot_status st = guarded(c, [&] {
         int dev = 0;
         MOT_CUDA_TRY(cudaGetDevice(&dev));
+        c->device = dev;
         MOT_CUDA_TRY(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
+        mot::excitation_setup(dev);
         MOT_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         const int N[3] = {c->U, c->V, c->W};
         for (int a = 0; a < 3; ++a) mot::fft_plan_axis(c->ax[a], pad_size(N[a]));
@@ -369,6 +371,7 @@ mot_status mot_create_shared(mot_ctx* src, mot_ctx** out) {
     }
     c->smax = src->smax;
     c->nsm = src->nsm; c->cg_blocks = src->cg_blocks;
+    c->device = src->device;
     c->shared_src = src;
     src->n_shared += 1;
     const long long M = c->M;
@@ -592,6 +595,13 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
             if (std::isfinite(v)) c->peak_norm = std::max(c->peak_norm, v);
             c->last_norm = v;
         }
+        if (result == MOT_OK && (hs[1] & 2)) {   // non-finite solve (the norm check above
+            result = MOT_ERR_UNSTABLE;             // catches it too; kept for clarity)
+            if (!c->fail_step) c->fail_step = hs[2];
+            char b[160];
+            snprintf(b, sizeof b, "unstable: NaN or Inf in the solve of step %d", hs[2]);
+            c->err = b;
+        }
         if (result == MOT_OK && (hs[1] & 1)) {
             result = MOT_ERR_NOT_CONVERGED;
             if (!c->fail_step) c->fail_step = hs[2];
@@ -768,12 +778,12 @@ mot_status mot_adjoint_run(mot_ctx* c, int n_count, const double* J_win, int win
                                          cudaMemcpyDeviceToHost, s));
         MOT_CUDA_TRY(cudaStreamSynchronize(s));
         c->adj_done += n_count;
-        if (hs[1] & 1) {
-            result = MOT_ERR_NOT_CONVERGED;
-            c->err = "adjoint: CG did not converge";
-        } else if (hs[1] & 2) {
+        if (hs[1] & 2) {
             result = MOT_ERR_UNSTABLE;
             c->err = "adjoint: NaN or Inf in lambda";
+        } else if (hs[1] & 1) {
+            result = MOT_ERR_NOT_CONVERGED;
+            c->err = "adjoint: CG did not converge";
         }
     });
     for (void* p : owned) cudaFree(p);

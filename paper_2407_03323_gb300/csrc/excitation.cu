@@ -17,10 +17,12 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace {
 
 constexpr int NQ = 6;
+constexpr int kMaxSetupDevices = 64;
 __constant__ double c_qx[NQ], c_qw[NQ];
 
 __global__ void k_plane_wave(long long M, int U, int V, const double* __restrict__ chi, double kx,
@@ -115,8 +117,15 @@ __global__ void k_plane_wave_tab(long long M, int U, int V, const double* __rest
 
 namespace mot {
 
-void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, double st, double t0,
-                int n_first, int n_steps, double* Edev, cudaStream_t s) {
+void excitation_setup(int dev) {
+    // the __constant__ nodes live once per device and module: upload them the first
+    // time a context is created on `dev` (a blocking copy, kept out of the per-call path)
+    static std::mutex mu;
+    static bool done[kMaxSetupDevices] = {};
+    if (dev < 0 || dev >= kMaxSetupDevices)
+        throw MotError{MOT_ERR_ARG, "device index beyond the supported range"};
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
     // Gauss-Legendre nodes on [-1/2, 1/2] (weights sum to 1)
     double x[NQ], w[NQ];
     {
@@ -141,6 +150,11 @@ void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, dou
     }
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_qx, x, sizeof x));
     MOT_CUDA_TRY(cudaMemcpyToSymbol(c_qw, w, sizeof w));
+    done[dev] = true;
+}
+
+void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, double st, double t0,
+                int n_first, int n_steps, double* Edev, cudaStream_t s) {
     if (!c->pw_tab) {   // no table buffer: the tensor rule at every voxel and step
         const long long tot = c->M * n_steps;
         k_plane_wave<<<(int)((tot + 255) / 256), 256, 0, s>>>(c->M, c->U, c->V, c->chi, k[0], k[1],

@@ -19,10 +19,10 @@
 // Toeplitz product by overlap-save: per spectral bin a length-2S FFT over time of the
 // window Jhat(n0 - 2S .. n0 - 1) (read from the ring), a product with the precomputed
 // temporal spectrum of [Ghat_S .. Ghat_{2S-1}, 0 .. 0], an inverse FFT, and the last
-// S outputs added into a ring of future-history accumulators.  Every time is covered
-// by exactly one firing of the largest level, which happens no later than any other
-// firing covering it; that level writes the accumulators and the others add to them.
-// The per-step near MAC adds the accumulator of its step.  A level's inputs are all older than n0,
+// S outputs written to that level's own ring of future-history accumulators (S slots).
+// Every time is covered by exactly one firing of each level, so a firing only stores
+// (no read-modify-write), and the per-step near MAC adds every level's entry for its
+// step.  A level's inputs are all older than n0,
 // so the scheme is causal (the division of Sec. 4.1 into Toeplitz blocks that use only
 // computed currents); levels double in length so a step costs O(log ell) block work on
 // average, the temporal counterpart of Eq. ComplexityHierarchicalDivisionInTime.

@@ -34,6 +34,7 @@ struct MotError {
     do {                                                                              \
         cudaError_t e_ = (expr);                                                      \
         if (e_ != cudaSuccess) {                                                      \
+            cudaGetLastError(); /* clear a non-sticky error (e.g. a failed malloc) */ \
             char b_[512];                                                             \
             snprintf(b_, sizeof b_, "%s failed at %s:%d: %s", #expr, __FILE__,        \
                      __LINE__, cudaGetErrorString(e_));                               \
@@ -168,6 +169,7 @@ struct mot_ctx {
     std::vector<cudaEvent_t> events;   // 6 per step of the current call
 
     cudaStream_t stream = nullptr;
+    int device = 0;              // CUDA device the context was created on
 
     // mot_create_shared: setup (geometry, table, spectra, twiddles) borrowed from
     // shared_src, which must outlive this context; n_shared counts the borrowers
@@ -225,6 +227,7 @@ void adjoint_step(mot_ctx* c, int tau, int n, const double* g_aos, const double*
                   int j_first, double* grad_chi, double* lam_out, double* norm2_out,
                   cudaStream_t s);
 // excitation.cu
+void excitation_setup(int dev);   // once per device: Gauss nodes of the voxel average
 void plane_wave(mot_ctx* c, const double k[3], const double p[3], double fc, double st,
                 double t0, int n_first, int n_steps, double* Edev, cudaStream_t s);
 

@@ -12,7 +12,9 @@
 //
 // The scratch array is resolved once per device (cudaGetSymbolAddress with that
 // device current) on the first call there; that first call may also load the module,
-// so make it before any stream capture on that device.  Nothing in the scratch needs
+// so make it before any stream capture on that device.  Each call runs on the device
+// the context was created on (made current for the call, the caller's device restored
+// afterwards), whichever device is current when it is made.  Nothing in the scratch needs
 // to start at zero: the kernel writes every element that the copy then reads.  There
 // is one scratch array per device per process, so calls that overlap in time (from
 // several host threads, on any contexts of the same device) overwrite each other's
@@ -78,14 +80,27 @@ extern "C" mot_status mot_plane_wave_static(mot_ctx* c, const double k_hat[3],
                  "destination";
         return MOT_ERR_ARG;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        c->err = "mot_plane_wave_static: no usable current device";
+    // the context's device, made current for the call (and the caller's restored):
+    // the scratch address and the launches must both belong to it
+    if (c->device < 0 || c->device >= kMaxDevices) {
+        c->err = "mot_plane_wave_static: context device beyond the supported range";
+        return MOT_ERR_ARG;
+    }
+    int caller_dev = 0;
+    cudaError_t e = cudaGetDevice(&caller_dev);
+    if (e == cudaSuccess && caller_dev != c->device) e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->err = std::string("mot_plane_wave_static: cannot select the context's device: ") +
+                 cudaGetErrorString(e);
         return MOT_ERR_CUDA;
     }
+    struct Restore {
+        int dev, prev;
+        ~Restore() { if (dev != prev) cudaSetDevice(prev); }
+    } restore{c->device, caller_dev};
     double* scratch = nullptr;
-    e = scratch_on(dev, &scratch);
+    e = scratch_on(c->device, &scratch);
     if (e != cudaSuccess) {
         cudaGetLastError();
         c->err = std::string("mot_plane_wave_static: cudaGetSymbolAddress failed: ") +

@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
     double* red1 = a.red + nb;
     double bb = 0.0, rr = 0.0;
     int its = 0, outer = 0;
-    bool first = true, converged = false, zeroed = false;
+    bool first = true, converged = false, zeroed = false, nonfinite = false;
     if (DF) {
         for (long long i = t0; i < a.nact; i += gs) {
             const int m = a.act[i];
@@ -584,6 +584,17 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         if (first) bb = grid_total(red1, nb);
         first = false;
         grid.sync();   // all blocks have read red0/red1
+        if (!(rr <= 1e300) || !(bb <= 1e300)) {
+            // NaN or Inf in the right-hand side (or the start): no iteration can help;
+            // J_n is returned as NaN so that the monitor and the caller see it
+            const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+            for (long long i = t0; i < a.nact; i += gs) {
+                const int m = a.act[i];
+                a.x[m] = qnan; a.x[M + m] = qnan; a.x[2 * M + m] = qnan;
+            }
+            nonfinite = true;
+            break;
+        }
         if (bb == 0.0) {
             for (long long i = t0; i < a.nact; i += gs) {
                 const int m = a.act[i];
@@ -594,7 +605,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
             break;
         }
         if (rr <= a.tol2 * bb) { converged = true; break; }
-        if (!(rr == rr) || outer >= a.max_outer || its >= a.max_iter) break;
+        if (outer >= a.max_outer || its >= a.max_iter) break;
         // ---- FP32 Chebyshev iteration for A e = r / ||r|| (r holds the FP32 residual).
         // One fused pass per iteration (apply to d_k, update e, r, d_{k+1}) and one grid
         // barrier; d is double-buffered because neighbours read d_k during the pass.
@@ -656,7 +667,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         grid.sync();
         ++outer;
     }
-    if (DF && !zeroed) {   // x = hi + lo back in FP64
+    if (DF && !zeroed && !nonfinite) {   // x = hi + lo back in FP64
         for (long long i = t0; i < a.nact; i += gs) {
             const int m = a.act[i];
             const float4 h = a.xh[m], l = a.xl[m];
@@ -666,6 +677,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         }
         grid.sync();
     }
+    if (zeroed || nonfinite) grid.sync();   // x written above is read by other blocks below
     // norm of the solution (all voxels, active and not)
     double xx = 0.0, dummy = 0.0;
     for (long long m = t0; m < M; m += gs)
@@ -679,8 +691,8 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         *a.norm2 = nx;
         a.status[0] = its;
         int flag = 0;
-        if (!converged) flag |= 1;                      // not converged (or NaN)
-        if (!(nx == nx) || nx > 1e300) flag |= 2;       // NaN / Inf
+        if (!converged && !nonfinite) flag |= 1;        // not converged
+        if (nonfinite || !(nx == nx) || nx > 1e300) flag |= 2;   // NaN / Inf
         if (flag && a.status[2] == 0) a.status[2] = a.step;
         a.status[1] |= flag;
         a.status[3] += its;

@@ -33,7 +33,7 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
-           "mot_frequency_response", "mot_last_error"]
+           "mot_frequency_response", "mot_fma_peak", "mot_last_error"]
 MOT_PDSA_FP32_SPECTRUM = 1
 MOT_PDSA_FULL_REORTH = 2
 
@@ -93,6 +93,7 @@ def load_library(path=LIB_PATH):
     lib.mot_truncate_table.argtypes = [P, D]
     lib.mot_fir_magnitude.argtypes = [P, I, I, P, P]
     lib.mot_frequency_response.argtypes = [I, I, P, D, D, P, D, D, I, P, P, P]
+    lib.mot_fma_peak.argtypes = [I, I, P, P]
     lib.mot_last_error.argtypes = [P]
     lib.mot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -166,6 +167,23 @@ def frequency_response(J, dt, taper, eps_probe, f_c, sigma_t, freqs, with_spectr
     if st != MOT_OK:
         raise MotError(st, "mot_frequency_response failed")
     return (H, jh) if with_spectrum else H
+
+
+def fma_peak(fp64=True, target_ms=100.0):
+    """Sustained FMA rate of the current device in FLOP/s (mot_fma_peak), from one launch
+    sized to take about target_ms after a short calibration launch."""
+    lib = load_library()
+    ms = ctypes.c_float()
+    fl = ctypes.c_double()
+    iters = 2048
+    for _ in range(3):
+        st = lib.mot_fma_peak(1 if fp64 else 0, iters, ctypes.byref(ms), ctypes.byref(fl))
+        if st != MOT_OK:
+            raise MotError(st, "mot_fma_peak failed")
+        if ms.value >= 0.5 * target_ms:
+            break
+        iters = int(min(2 ** 30, iters * target_ms / max(ms.value, 1e-3)))
+    return fl.value / (ms.value * 1e-3)
 
 
 class Context:
@@ -251,11 +269,30 @@ class Context:
         n = E.shape[0]
         self._check(self._lib.mot_set_excitation(self._h, n, _ptr(E), _stream(stream)))
 
+    def _check_out(self, out, n_steps, host_only=False):
+        """The C side writes n_steps * M * 3 doubles to `out`: refuse anything else."""
+        is_np = isinstance(out, np.ndarray)
+        if host_only and not (is_np or (hasattr(out, "device") and
+                                        str(getattr(out, "device")) == "cpu")):
+            raise TypeError("out must be host memory (a numpy array or a CPU tensor)")
+        if not is_np and not hasattr(out, "data_ptr"):
+            raise TypeError("out must be a numpy array or a torch tensor")
+        if not _dtype_ok(out) or getattr(out, "dtype", None) is None:
+            raise TypeError("out must be float64")
+        size = out.size if is_np else out.numel()
+        if size != n_steps * self.M * 3:
+            raise ValueError("out holds %d values, %d needed ([n_steps][M][3])"
+                             % (size, n_steps * self.M * 3))
+        contiguous = out.flags["C_CONTIGUOUS"] if is_np else out.is_contiguous()
+        if not contiguous:
+            raise ValueError("out must be C-contiguous")
+
     def plane_wave(self, k_hat, p_hat, f_c, sigma_t, t0, n_first, n_steps, out=None, stream=None):
         """Tested modulated-Gaussian plane wave E[n_steps][M][3] of steps n_first..
         (mot_plane_wave, Eq. E); out: numpy array or CUDA tensor, else a new array."""
         if out is None:
             out = np.zeros((n_steps, self.M, 3))
+        self._check_out(out, n_steps)
         k = np.ascontiguousarray(k_hat, dtype=np.float64)
         p = np.ascontiguousarray(p_hat, dtype=np.float64)
         self._check(self._lib.mot_plane_wave(self._h, k.ctypes.data, p.ctypes.data, f_c, sigma_t,
@@ -268,6 +305,7 @@ class Context:
         the library's fixed device scratch instead of a per-call allocation."""
         if out is None:
             out = np.zeros((n_steps, self.M, 3))
+        self._check_out(out, n_steps, host_only=True)
         k = np.ascontiguousarray(k_hat, dtype=np.float64)
         p = np.ascontiguousarray(p_hat, dtype=np.float64)
         self._check(self._lib.mot_plane_wave_static(self._h, k.ctypes.data, p.ctypes.data, f_c,

@@ -107,3 +107,39 @@ def test_tiny_and_huge_excitations_scale_linearly(mot, precision, factors, tol):
     for f in factors:
         assert np.isfinite(res[f]).all()
         assert np.linalg.norm(res[f] / f - res[1.0]) < tol * np.linalg.norm(res[1.0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_history"])
+def test_nan_in_excitation_is_unstable_at_its_step(mot, precision):
+    """A NaN placed by the host in E_k (one component of one voxel): the solve of step k
+    stops on the non-finite residual instead of iterating, returns J_k as NaN, and the
+    monitor reports MOT_ERR_UNSTABLE with fail_step = k; the steps before k are finite."""
+    k = 17
+    eps = wl.cube(6, 5.0)
+    p = wl.pulse(6, 5.0)
+    with mot.Context(eps, precision=precision) as ctx:
+        E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 60, 1, 32)
+        E[k - 1, 100, 1] = np.nan
+        ctx.set_excitation(E)
+        J = np.zeros((32, ctx.M, 3))
+        with pytest.raises(mot.MotError) as ei:
+            ctx.march(32, out=J)
+        assert ei.value.status == mot.MOT_ERR_UNSTABLE
+        info = ctx.info()
+        assert info["fail_step"] == k
+        assert info["n_done"] == 32
+        assert np.isfinite(J[:k - 1]).all()
+        assert not np.isfinite(J[k - 1]).all()
+
+
+def test_grid_too_large_for_the_device_is_oom(mot):
+    """A 1024 x 1024 x 1 grid (ell = 1450, padded 2048 x 2048 x 2) needs a 292 GB FP64
+    spectral ring, more than the device holds: mot_create returns MOT_ERR_OOM, frees
+    what it had allocated, and the next context works."""
+    eps = np.full((1, 1024, 1024), 2.0)
+    with pytest.raises(mot.MotError) as ei:
+        mot.Context(eps)
+    assert ei.value.status == mot.MOT_ERR_OOM
+    with mot.Context(wl.cube(4, 3.0)) as ctx:
+        ctx.march(4)
+        assert ctx.info()["n_done"] == 4
