@@ -14,8 +14,13 @@ Contents (each function cites the passage of the paper it follows):
                     Eq. TDJVIE), cylindrical tanh-sinh route
 * ``static``        static (lag-summed) element integrals by an independent
                     Cartesian tensor-Gauss/Duffy route; used only to pin the table
+* ``brute``         every lag and component of the elements by a Cartesian iterated
+                    rule that resolves the shells r = integer; used only to pin the table
 * ``excitation``    tested incident field (Eq. E) for the modulated Gaussian plane wave
-* ``march``         direct space-time sum (Eq. PnMOT) + dense Z_0 solve (Eq. MOTInversion)
+* ``march``         direct space-time sum (Eq. PnMOT) + dense Z_0 solve (Eq. MOTInversion);
+                    sparse-source history from per-offset elements
+* ``direct``        the same march with the history summed by plain C loops over voxel
+                    pairs and lags (``direct_sum.c``) for grids whose dense Z_l do not fit
 * ``pdsa``          PDSA matrices D_n (Eq. Dn), the FIR regularisation identity, and the
                     spectrum bracket of D_n from its circulant embedding (App. A; numpy
                     FFT of the embedded kernel, 3x3 eigenvalues per bin)

@@ -1,25 +1,25 @@
-"""Independent Cartesian routes to element integrals, used only to pin ``kernel_table``.
+"""Independent Cartesian route to the lag-summed element integrals, used only to pin
+``kernel_table``.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-Two routes that share nothing with the cylindrical construction of ``kernel_table``:
+It shares nothing with the cylindrical construction of ``kernel_table``.
 
-1. Static (lag-summed) integrals.  Because T is a partition of unity that reproduces
-   polynomials up to degree 2 (sum_l T(l - r) = 1, sum_l l T(l - r) = r + 1/2,
-   sum_l l^2 T(l - r) = r^2 + r + 1/2), the lag moments of the table reduce to static
-   integrals over the voxel autocorrelation C_d (Eq. Z summed over n - n'):
+Static (lag-summed) integrals.  Because T is a partition of unity that reproduces
+polynomials up to degree 2 (sum_l T(l - r) = 1, sum_l l T(l - r) = r + 1/2,
+sum_l l^2 T(l - r) = r^2 + r + 1/2), the lag moments of the table reduce to static
+integrals over the voxel autocorrelation C_d (Eq. Z summed over n - n'):
 
-       sum_l l^2 K^vol_l(d)      = 2 int C_d / (4 pi r)                 = 2 S(d)
-       sum_l K^face_l^{ab}(d)    = int d_a d_b C_d / (4 pi r)           = F^{ab}(d)
-       sum_l l K^face_l^{ab}(d)  = F^{ab}(d) / 2
-       sum_l l^2 K^face_l^{ab}(d)= int d_a d_b C_d r / (4 pi) + F^{ab}(d) / 2
+    sum_l l^2 K^vol_l(d)      = 2 int C_d / (4 pi r)                 = 2 S(d)
+    sum_l K^face_l^{ab}(d)    = int d_a d_b C_d / (4 pi r)           = F^{ab}(d)
+    sum_l l K^face_l^{ab}(d)  = F^{ab}(d) / 2
+    sum_l l^2 K^face_l^{ab}(d)= int d_a d_b C_d r / (4 pi) + F^{ab}(d) / 2
 
-   computed here by tensor Gauss-Legendre on the unit cells of C_d, with a Duffy
-   (pyramid) map on cells that have the 1/r singularity at a corner.
+computed here by tensor Gauss-Legendre on the unit cells of C_d, with a Duffy
+(pyramid) map on cells that have the 1/r singularity at a corner.
 
-2. Brute force per lag: recursive subdivision of the cells, tensor Gauss on every
-   leaf (the shells r = integer are not resolved, so this converges only
-   algebraically; it is a coarse, fully independent check of each lag).
+Each lag and component on its own is pinned by ``brute`` (a Cartesian iterated rule
+that resolves the shells r = integer).
 """
 import functools
 import itertools
@@ -153,30 +153,3 @@ def static_face(d, a, b, moment=-1, n=20):
         for lo in [(d[p] + i, d[q] + j) for i in (-1.0, 0.0) for j in (-1.0, 0.0)]:
             total += we * _cell_integral2(w2, f, h, lo, n)
     return total
-
-
-# ------------------------------------------------------------- brute force per lag
-
-def brute_force_vol(d, nlag, depth=5, n=4):
-    """K^vol_l(d) by recursive 2^depth subdivision of each cell and an n^3 Gauss rule
-    per leaf, with the discontinuous T'' evaluated pointwise (coarse, O(leaf) error)."""
-    from .spline import T2
-    d = tuple(float(v) for v in d)
-    xg, wg = _gl(n)
-    m = 2 ** depth
-    h = 1.0 / m
-    loc = (np.arange(m)[:, None] * h + 0.5 * h * (xg[None, :] + 1.0)).ravel()
-    wl = np.tile(0.5 * h * wg, m)
-    out = np.zeros(nlag)
-    for lo in _support_cells(d):
-        X = lo[0] + loc[:, None, None]
-        Y = lo[1] + loc[None, :, None]
-        Z = lo[2] + loc[None, None, :]
-        X, Y, Z = np.broadcast_arrays(X, Y, Z)
-        W = wl[:, None, None] * wl[None, :, None] * wl[None, None, :]
-        C = _hat(X, d[0]) * _hat(Y, d[1]) * _hat(Z, d[2])
-        r = np.sqrt(X * X + Y * Y + Z * Z)
-        base = W * C / (FOUR_PI * r)
-        for l in range(nlag):
-            out[l] += float(np.sum(base * T2(l - r)))
-    return out

@@ -363,8 +363,19 @@ __global__ void quad_kernel(const int3* __restrict__ triples, int ntriples,
     }
 }
 
+// Rank of a sorted triple a >= b >= c among the triples a grid needs: with the grid's
+// sides sorted L1 >= L2 >= L3, exactly those with a < L1, b < L2, c < L3 (the k-th
+// largest offset coordinate is below the k-th largest side), enumerated by a, then b,
+// then c.  For a given b there are min(b, L3 - 1) + 1 values of c, so the triples with
+// first b' < b number g(b) = b (b + 1) / 2 (b <= L3), L3 (L3 + 1) / 2 + (b - L3) L3
+// (b > L3); off_a[a] counts the triples with first coordinate below a.
+__host__ __device__ inline long long tri_before_b(long long b, long long L3) {
+    return b <= L3 ? b * (b + 1) / 2 : L3 * (L3 + 1) / 2 + (b - L3) * L3;
+}
+
 // octant assembly: G_l^{ab}(d) = K^face^{ab} - delta_ab K^vol, windowed in lag
 __global__ void assemble_kernel(const double* __restrict__ res, int U, int V, int W,
+                                const long long* __restrict__ off_a, int L3,
                                 int* __restrict__ tab_l0, double* __restrict__ tab) {
     const long long oct = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)U * V * W;
@@ -380,7 +391,7 @@ __global__ void assemble_kernel(const double* __restrict__ res, int U, int V, in
     int p[3];
     for (int k = 0; k < 3; ++k) p[order[k]] = k;
     const long long a = key[0], b = key[1], c = key[2];
-    const long long t = a * (a + 1) * (a + 2) / 6 + b * (b + 1) / 2 + c;
+    const long long t = off_a[a] + tri_before_b(b, L3) + c;
     const double* r0 = res + (t * 3 + 0) * 3 * mot::WIN;   // axis z pass
     const double* r1 = res + (t * 3 + 1) * 3 * mot::WIN;   // axis x pass
     const double* r2 = res + (t * 3 + 2) * 3 * mot::WIN;   // axis y pass
@@ -420,16 +431,25 @@ void compute_table(mot_ctx* c) {
         MOT_CUDA_TRY(cudaMemcpyToSymbol(c_gz_x, t.data(), sizeof(double) * NZ));
         MOT_CUDA_TRY(cudaMemcpyToSymbol(c_gz_w, w.data(), sizeof(double) * NZ));
     }
-    const int nmax = std::max(c->U, std::max(c->V, c->W));
+    // the sorted offsets a >= b >= c that occur in this grid (see tri_before_b)
+    int L[3] = {c->U, c->V, c->W};
+    std::sort(L, L + 3, [](int x, int y) { return x > y; });
     std::vector<int3> tri;
-    for (int a = 0; a < nmax; ++a)
-        for (int b = 0; b <= a; ++b)
-            for (int cc = 0; cc <= b; ++cc) tri.push_back(make_int3(a, b, cc));
+    std::vector<long long> off_a(L[0]);
+    for (int a = 0; a < L[0]; ++a) {
+        off_a[a] = (long long)tri.size();
+        for (int b = 0; b <= std::min(a, L[1] - 1); ++b)
+            for (int cc = 0; cc <= std::min(b, L[2] - 1); ++cc) tri.push_back(make_int3(a, b, cc));
+    }
     const int nt = (int)tri.size();
     int3* dtri = nullptr;
     double* dres = nullptr;
     int* derr = nullptr;
+    long long* doff = nullptr;
     try {
+        MOT_CUDA_TRY(cudaMalloc(&doff, sizeof(long long) * L[0]));
+        MOT_CUDA_TRY(cudaMemcpyAsync(doff, off_a.data(), sizeof(long long) * L[0],
+                                     cudaMemcpyHostToDevice, c->stream));
         MOT_CUDA_TRY(cudaMalloc(&dtri, sizeof(int3) * nt));
         MOT_CUDA_TRY(cudaMalloc(&dres, sizeof(double) * (size_t)nt * 3 * 3 * WIN));
         MOT_CUDA_TRY(cudaMalloc(&derr, sizeof(int)));
@@ -443,8 +463,8 @@ void compute_table(mot_ctx* c) {
         const long long noff = (long long)c->U * c->V * c->W;
         MOT_CUDA_TRY(cudaMalloc(&c->tab_l0, sizeof(int) * noff));
         MOT_CUDA_TRY(cudaMalloc(&c->tab, sizeof(double) * noff * 6 * WIN));
-        assemble_kernel<<<(int)((noff + 255) / 256), 256, 0, c->stream>>>(dres, c->U, c->V, c->W,
-                                                                          c->tab_l0, c->tab);
+        assemble_kernel<<<(int)((noff + 255) / 256), 256, 0, c->stream>>>(
+            dres, c->U, c->V, c->W, doff, L[2], c->tab_l0, c->tab);
         MOT_LAUNCH_CHECK();
         int herr = 0;
         MOT_CUDA_TRY(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -454,11 +474,13 @@ void compute_table(mot_ctx* c) {
         cudaFree(dtri);
         cudaFree(dres);
         cudaFree(derr);
+        cudaFree(doff);
         throw;
     }
     cudaFree(dtri);
     cudaFree(dres);
     cudaFree(derr);
+    cudaFree(doff);
 }
 
 }  // namespace mot

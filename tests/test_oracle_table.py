@@ -122,15 +122,64 @@ def test_largest_lag_is_ell():
     assert nz[-1] == ell
 
 
-@pytest.mark.parametrize("d", [(1, 0, 0), (2, 1, 1)])
-def test_brute_force_per_lag(d):
-    """Each lag against a brute-force subdivided tensor-Gauss rule (coarse: the
-    shells are not resolved, the error is ~1e-4 of the largest element; a shifted
-    lag, dropped piece or wrong sign shows up at order one)."""
-    nl = 7
-    vol, _ = kt.offset_elements(d, nl)
-    bf = static.brute_force_vol(d, nl, depth=5)
-    assert np.abs(vol - bf).max() < 1e-3 * np.abs(vol).max()
+BRUTE_OFFSETS = [(0, 0, 0), (1, 0, 0), (1, 1, 0), (2, 1, 1), (3, 2, 1), (5, 5, 4)]
+
+
+@pytest.mark.parametrize("d", BRUTE_OFFSETS)
+def test_every_lag_and_component_against_cartesian_rule(d):
+    """Each lag of K^vol and of all nine K^face components (off-diagonal ones included)
+    against the independent Cartesian iterated rule of ``brute`` that resolves every
+    shell r = k (no cylinder, arcs or tanh-sinh): equal to 1e-9 of the largest element
+    at that offset (the Cartesian rule itself is converged to ~1e-12 at 16 nodes per
+    piece; see the next test)."""
+    from oracle import brute
+    nl = 12
+    vol, face = kt.offset_elements(d, nl)
+    bv, bf = brute.element_lags(d, nl, n=16)
+    scale = max(np.abs(vol).max(), np.abs(face).max())
+    assert np.abs(vol - bv).max() < 1e-9 * scale
+    for a, b in itertools.product(range(3), range(3)):
+        assert np.abs(face[a, b] - bf[a, b]).max() < 1e-9 * scale, (a, b)
+
+
+def test_cartesian_rule_converged():
+    """The Cartesian rule at 12 and at 20 nodes per piece agrees to 1e-8 of the largest
+    element (its error decays geometrically once the shells are resolved)."""
+    from oracle import brute
+    for d in ((1, 0, 0), (2, 1, 1)):
+        v0, f0 = brute.element_lags(d, 10, n=12)
+        v1, f1 = brute.element_lags(d, 10, n=20)
+        scale = max(np.abs(v1).max(), np.abs(f1).max())
+        assert np.abs(v0 - v1).max() < 1e-8 * scale
+        assert np.abs(f0 - f1).max() < 1e-8 * scale
+
+
+def test_moment_preserving_lag_error_is_caught(monkeypatch):
+    """A mistake planted in the oracle that moves weight of the Lam'Lam' (xy) component
+    between four neighbouring lags as eps (1, -3, 3, -1), which keeps the lag moments of
+    order 0, 1, 2 and the trace (the other pins), is caught by the per-lag comparison."""
+    from oracle import brute
+    d, nl = (2, 1, 1), 12
+    good = kt.offset_elements
+
+    def planted(dd, nlag, *a, **k):
+        vol, face = good(dd, nlag, *a, **k)
+        eps = 1e-6 * np.abs(face).max()
+        pat = eps * np.array([1.0, -3.0, 3.0, -1.0])
+        face = face.copy()
+        face[0, 1, 2:6] += pat
+        face[1, 0, 2:6] += pat
+        return vol, face
+
+    monkeypatch.setattr(kt, "offset_elements", planted)
+    vol, face = kt.offset_elements(d, nl)
+    vol0, face0 = good(d, nl)
+    l = np.arange(nl)
+    for k in range(3):                 # the moment pins cannot see it
+        assert abs(((l ** k) * (face[0, 1] - face0[0, 1])).sum()) < 1e-15
+    bv, bf = brute.element_lags(d, nl, n=16)
+    scale = max(np.abs(vol).max(), np.abs(face).max())
+    assert np.abs(face[0, 1] - bf[0, 1]).max() > 1e-7 * scale
 
 
 def test_rule_refinement_converged():
