@@ -860,6 +860,212 @@ void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     MOT_LAUNCH_CHECK();
 }
 
+// ---------------------------------------------------------------- FP32 far levels
+// The block product of one level firing with the four-step transform of length
+// P = Q1 T (Q1 = 16, T = P / 16 = 1 .. 16) in which every thread holds all three
+// components of its share of a temporal line: the 3x3 product then needs no exchange
+// between components, and every thread works in every phase.
+//   phase A: thread (t, bin) loads x[t + T n2], n2 < 16, of the three components (the
+//            window times n0 - P + t + T n2; zero before tfirst), runs the 16-point
+//            DFTs in registers (compile-time twiddles), multiplies by W_P^{t k2} and
+//            stores to shared memory;
+//   phase B: thread (tt, bin) takes k2 = tt, tt + T, ...: the T values of each
+//            component, T-point DFTs (frequency w = k2 + 16 k1), the 3x3 product with
+//            the level spectrum H(w) ([w][6][octant bin] in global memory, coalesced
+//            over consecutive bins; conj H(P - w) above S), inverse T-point DFTs and
+//            W_P^{-t k2}, back to shared memory;
+//   phase C: thread (t, bin) runs the inverse 16-point DFTs over k2 and stores
+//            y[t + T n2] for n2 >= 8, the last S = 8 T positions of the window.
+// With T = 1 (P = 16) one thread per bin does all of it in registers.  A CTA takes
+// NB = 128 / T consecutive octant bins (across rfft rows) and walks the four mirror
+// rows (ku, +-kv, +-kw) of each; a mirror that does not exist for a bin's row
+// (kv = 0 or Pv / 2, likewise kw) only skips that bin's loads and stores.  Mirror
+// signs: inputs and outputs of component b are scaled by sigma_b (sigma_x = 1,
+// sigma_y = -1 on a mirrored v, sigma_z = -1 on a mirrored w), so the octant spectra
+// serve every mirror.  Shared memory element (c, k2, t, bin) sits at
+// c CS + k2 KS + t NB + bin, KS padded for NB = 8 so that no phase has bank conflicts.
+template <int P> struct FarFS {
+    static constexpr int Q1 = 16, T = P / Q1, S = P / 2, NTH = 128, NB = NTH / T;
+    static constexpr int KS = T * NB + (NB < 16 ? 8 : 0);
+    static constexpr int CS = Q1 * KS;
+    static_assert(T >= 1 && T * Q1 == P && T <= 16, "far four-step shape");
+    // the level spectra of the CTA's bins, [w][c][bin], staged once for the four
+    // mirrors (copied asynchronously while the first window loads)
+    static constexpr int HS = (S + 1) * 6 * NB;
+    struct Smem {
+        float2 V[T > 1 ? 3 * CS : 2];
+        float2 H[HS];
+        float2 tw[P];          // W_P^m, m < P
+        int in[P];             // ring slot of every window time (-1: none)
+        int out[S];            // accumulator slot of every output time
+    };
+};
+
+template <int P>
+__global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> a) {
+    typedef FarFS<P> F;
+    constexpr int Q1 = F::Q1, T = F::T, S = F::S, NB = F::NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    typename F::Smem& sm = *reinterpret_cast<typename F::Smem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int bin = tid % NB, t = tid / NB;
+    const long long o = (long long)blockIdx.x * NB + bin;       // octant bin
+    const bool obin = o < a.noct;
+    const int ku = obin ? (int)(o % a.Hu) : 0;
+    const int kv_o = obin ? (int)((o / a.Hu) % a.Hv) : 0;
+    const int kw_o = obin ? (int)(o / ((long long)a.Hu * a.Hv)) : 0;
+    const bool mv = kv_o > 0 && 2 * kv_o < a.Pv;
+    const bool mw = kw_o > 0 && 2 * kw_o < a.Pw;
+    const int tfirst = max(1, a.n0 - a.lmax);
+    {   // H[w][c][bin] <- a.H[(w * 6 + c) * noct + o0 + bin], o0 the CTA's first bin
+        const long long o0 = (long long)blockIdx.x * NB;
+        for (int i = tid; i < F::HS; i += F::NTH) {
+            const int b = i % NB;
+            const bool ok = o0 + b < a.noct;
+            cp_async_c(&sm.H[i], ok ? a.H + (long long)(i / NB) * a.noct + o0 + b : a.H, ok);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    for (int i = tid; i < P; i += F::NTH) {
+        const int time = a.n0 - P + i;
+        sm.in[i] = time >= tfirst ? time % a.hring : -1;
+        sm.tw[i] = a.tw[i];
+        if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
+    }
+    __syncthreads();
+    for (int mirror = 0; mirror < 4; ++mirror) {
+        const bool fv = (mirror & 1) != 0, fw = (mirror & 2) != 0;
+        const bool live = obin && (!fv || mv) && (!fw || mw);
+        const int kv = fv ? a.Pv - kv_o : kv_o;
+        const int kw = fw ? a.Pw - kw_o : kw_o;
+        const long long bidx = ((long long)kw * a.Pv + kv) * a.Hu + ku;
+        const float sy = fv ? -1.f : 1.f, sz = fw ? -1.f : 1.f;
+        // ---- phase A: loads, 16-point DFTs over n2, twiddles W_P^{t k2}
+        float2 x[3][Q1];
+        Unroll<0, Q1>::run([&](auto q) {
+            constexpr int n2 = decltype(q)::value;
+            const int slot = sm.in[t + T * n2];
+            float2 v0 = make_float2(0.f, 0.f), v1 = v0, v2 = v0;
+            if (live && slot >= 0) {
+                const float2* src = a.ring + (long long)slot * 3 * a.nbins + bidx;
+                v0 = src[0];
+                v1 = src[a.nbins];
+                v2 = src[2 * a.nbins];
+            }
+            x[0][n2] = v0;
+            x[1][n2] = make_float2(sy * v1.x, sy * v1.y);
+            x[2][n2] = make_float2(sz * v2.x, sz * v2.y);
+        });
+        Unroll<0, 3>::run([&](auto cq) { dft_ct<Q1, -1>(x[decltype(cq)::value]); });
+        if constexpr (T == 1) {
+            // ---- the whole product in registers: frequency w = k2
+            if (mirror == 0) {
+                asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+                __syncthreads();
+            }
+            Unroll<0, Q1>::run([&](auto q) {
+                constexpr int w = decltype(q)::value;
+                constexpr bool cj = w > S;
+                constexpr int ws = cj ? P - w : w;
+                float2 h[6];
+#pragma unroll
+                for (int cc = 0; cc < 6; ++cc) {
+                    h[cc] = sm.H[(ws * 6 + cc) * NB + bin];
+                    if (cj) h[cc].y = -h[cc].y;
+                }
+                const float2 x0 = x[0][w], x1 = x[1][w], x2 = x[2][w];
+                x[0][w] = cadd(cadd(cmul(h[0], x0), cmul(h[3], x1)), cmul(h[4], x2));
+                x[1][w] = cadd(cadd(cmul(h[3], x0), cmul(h[1], x1)), cmul(h[5], x2));
+                x[2][w] = cadd(cadd(cmul(h[4], x0), cmul(h[5], x1)), cmul(h[2], x2));
+            });
+        } else {
+            Unroll<0, Q1>::run([&](auto q) {
+                constexpr int k2 = decltype(q)::value;
+                const float2 w = sm.tw[t * k2];
+                float2* dst = &sm.V[k2 * F::KS + t * NB + bin];
+                dst[0] = cmul(x[0][k2], w);
+                dst[F::CS] = cmul(x[1][k2], w);
+                dst[2 * F::CS] = cmul(x[2][k2], w);
+            });
+            if (mirror == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            __syncthreads();
+            // ---- phase B: T-point DFTs over t, product, inverse, conjugate twiddles
+            for (int j = 0; j < Q1 / T; ++j) {
+                const int k2 = t + T * j;
+                float2 v[3][T];
+                Unroll<0, T>::run([&](auto q) {
+                    constexpr int tt = decltype(q)::value;
+                    const float2* src = &sm.V[k2 * F::KS + tt * NB + bin];
+                    v[0][tt] = src[0];
+                    v[1][tt] = src[F::CS];
+                    v[2][tt] = src[2 * F::CS];
+                });
+                Unroll<0, 3>::run([&](auto cq) { dft_ct<T, -1>(v[decltype(cq)::value]); });
+                Unroll<0, T>::run([&](auto q) {
+                    constexpr int k1 = decltype(q)::value;
+                    const int w = k2 + Q1 * k1;
+                    const bool cj = w > S;
+                    const int ws = cj ? P - w : w;
+                    float2 h[6];
+#pragma unroll
+                    for (int cc = 0; cc < 6; ++cc) {
+                        h[cc] = sm.H[(ws * 6 + cc) * NB + bin];
+                        if (cj) h[cc].y = -h[cc].y;
+                    }
+                    const float2 x0 = v[0][k1], x1 = v[1][k1], x2 = v[2][k1];
+                    v[0][k1] = cadd(cadd(cmul(h[0], x0), cmul(h[3], x1)), cmul(h[4], x2));
+                    v[1][k1] = cadd(cadd(cmul(h[3], x0), cmul(h[1], x1)), cmul(h[5], x2));
+                    v[2][k1] = cadd(cadd(cmul(h[4], x0), cmul(h[5], x1)), cmul(h[2], x2));
+                });
+                Unroll<0, 3>::run([&](auto cq) { dft_ct<T, +1>(v[decltype(cq)::value]); });
+                Unroll<0, T>::run([&](auto q) {
+                    constexpr int tt = decltype(q)::value;
+                    const float2 w = cconj(sm.tw[tt * k2]);
+                    float2* dst = &sm.V[k2 * F::KS + tt * NB + bin];
+                    dst[0] = cmul(v[0][tt], w);
+                    dst[F::CS] = cmul(v[1][tt], w);
+                    dst[2 * F::CS] = cmul(v[2][tt], w);
+                });
+            }
+            __syncthreads();
+            // ---- phase C: gather over k2
+            Unroll<0, Q1>::run([&](auto q) {
+                constexpr int k2 = decltype(q)::value;
+                const float2* src = &sm.V[k2 * F::KS + t * NB + bin];
+                x[0][k2] = src[0];
+                x[1][k2] = src[F::CS];
+                x[2][k2] = src[2 * F::CS];
+            });
+            __syncthreads();   // the next mirror's phase A overwrites V
+        }
+        Unroll<0, 3>::run([&](auto cq) { dft_ct<Q1, +1>(x[decltype(cq)::value]); });
+        if (live) {
+            const float sc = 1.f / (float)P;
+            Unroll<Q1 / 2, Q1>::run([&](auto q) {
+                constexpr int n2 = decltype(q)::value;
+                const int pos = t + T * n2;                  // >= S
+                float2* dst = a.acc + (long long)sm.out[pos - S] * 3 * a.nbins + bidx;
+                dst[0] = make_float2(sc * x[0][n2].x, sc * x[0][n2].y);
+                dst[a.nbins] = make_float2(sy * sc * x[1][n2].x, sy * sc * x[1][n2].y);
+                dst[2 * a.nbins] = make_float2(sz * sc * x[2][n2].x, sz * sc * x[2][n2].y);
+            });
+        }
+    }
+}
+
+template <int P>
+void far_launch_fs(mot_ctx* c, FarArgs<float>& a, cudaStream_t s) {
+    typedef FarFS<P> F;
+    const int sm_bytes = (int)sizeof(typename F::Smem);
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far_fs<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      sm_bytes));
+    MOT_CUDA_TRY(cudaFuncSetAttribute(k_far_fs<P>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      100));
+    const long long blocks = (c->noct + F::NB - 1) / F::NB;
+    k_far_fs<P><<<(int)blocks, F::NTH, sm_bytes, s>>>(a);
+    MOT_LAUNCH_CHECK();
+}
+
 template <typename R>
 void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
     HistoryBuffers<R>& hb = hbuf<R>(c);
@@ -890,11 +1096,11 @@ void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
         switch (a.S) {
             case 2: far_launch_reg<R, 4, 1>(c, a, s); break;
             case 4: far_launch_reg<R, 8, 1>(c, a, s); break;
-            case 8: far_launch_reg<R, 16, 1>(c, a, s); break;
-            case 16: far_launch_reg<R, 32, 1>(c, a, s); break;
-            case 32: far_launch_4s<R, 64>(c, a, s); break;
-            case 64: far_launch_4s<R, 128>(c, a, s); break;
-            case 128: far_launch_4s<R, 256>(c, a, s); break;
+            case 8: far_launch_fs<16>(c, a, s); break;
+            case 16: far_launch_fs<32>(c, a, s); break;
+            case 32: far_launch_fs<64>(c, a, s); break;
+            case 64: far_launch_fs<128>(c, a, s); break;
+            case 128: far_launch_fs<256>(c, a, s); break;
             default: far_launch<R, 4>(c, a, s);
         }
     } else {
