@@ -879,7 +879,10 @@ void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
 // With T = 1 (P = 16) one thread per bin does all of it in registers.  A CTA takes
 // NB = 128 / T consecutive octant bins (across rfft rows) and walks the four mirror
 // rows (ku, +-kv, +-kw) of each; a mirror that does not exist for a bin's row
-// (kv = 0 or Pv / 2, likewise kw) only skips that bin's loads and stores.  Mirror
+// (kv = 0 or Pv / 2, likewise kw) only skips that bin's loads and stores.  The level
+// spectra of the CTA's bins are staged in shared memory once for the four mirrors
+// (they were the loads the product waited on), and for T > 1 the next mirror's window
+// is loaded into the phase-A registers while phases B and C of the current one run.  Mirror
 // signs: inputs and outputs of component b are scaled by sigma_b (sigma_x = 1,
 // sigma_y = -1 on a mirrored v, sigma_z = -1 on a mirrored w), so the octant spectra
 // serve every mirror.  Shared memory element (c, k2, t, bin) sits at
@@ -890,8 +893,10 @@ template <int P> struct FarFS {
     static constexpr int CS = Q1 * KS;
     static_assert(T >= 1 && T * Q1 == P && T <= 16, "far four-step shape");
     // the level spectra of the CTA's bins, [w][c][bin], staged once for the four
-    // mirrors (copied asynchronously while the first window loads)
-    static constexpr int HS = (S + 1) * 6 * NB;
+    // mirrors (copied asynchronously while the first window loads); rows of one
+    // frequency padded when NB = 8, where the lanes of a half-warp read two frequencies
+    static constexpr int HW = 6 * NB + (NB < 16 ? 8 : 0);
+    static constexpr int HS = (S + 1) * HW;
     struct Smem {
         float2 V[T > 1 ? 3 * CS : 2];
         float2 H[HS];
@@ -902,7 +907,7 @@ template <int P> struct FarFS {
 };
 
 template <int P>
-__global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> a) {
+__global__ void __launch_bounds__(128, P <= 16 ? 4 : 2) k_far_fs(FarArgs<float> a) {
     typedef FarFS<P> F;
     constexpr int Q1 = F::Q1, T = F::T, S = F::S, NB = F::NB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -919,10 +924,11 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
     const int tfirst = max(1, a.n0 - a.lmax);
     {   // H[w][c][bin] <- a.H[(w * 6 + c) * noct + o0 + bin], o0 the CTA's first bin
         const long long o0 = (long long)blockIdx.x * NB;
-        for (int i = tid; i < F::HS; i += F::NTH) {
-            const int b = i % NB;
+        for (int i = tid; i < (S + 1) * 6 * NB; i += F::NTH) {
+            const int b = i % NB, wc = i / NB;                 // wc = w * 6 + c
             const bool ok = o0 + b < a.noct;
-            cp_async_c(&sm.H[i], ok ? a.H + (long long)(i / NB) * a.noct + o0 + b : a.H, ok);
+            cp_async_c(&sm.H[(wc / 6) * F::HW + (wc % 6) * NB + b],
+                       ok ? a.H + (long long)wc * a.noct + o0 + b : a.H, ok);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
@@ -933,15 +939,22 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
         if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
     }
     __syncthreads();
-    for (int mirror = 0; mirror < 4; ++mirror) {
-        const bool fv = (mirror & 1) != 0, fw = (mirror & 2) != 0;
-        const bool live = obin && (!fv || mv) && (!fw || mw);
+    // mirror m of the bin: whether it exists, its rfft bin, the signs sigma_y, sigma_z
+    auto mirror_of = [&](int m, bool& live, long long& bidx, float& sy, float& sz) {
+        const bool fv = (m & 1) != 0, fw = (m & 2) != 0;
+        live = obin && (!fv || mv) && (!fw || mw);
         const int kv = fv ? a.Pv - kv_o : kv_o;
         const int kw = fw ? a.Pw - kw_o : kw_o;
-        const long long bidx = ((long long)kw * a.Pv + kv) * a.Hu + ku;
-        const float sy = fv ? -1.f : 1.f, sz = fw ? -1.f : 1.f;
-        // ---- phase A: loads, 16-point DFTs over n2, twiddles W_P^{t k2}
-        float2 x[3][Q1];
+        bidx = ((long long)kw * a.Pv + kv) * a.Hu + ku;
+        sy = fv ? -1.f : 1.f;
+        sz = fw ? -1.f : 1.f;
+    };
+    // window samples x[t + T n2], n2 < Q1, of the three components (sigma-scaled)
+    auto load_window = [&](int m, float2 (&x)[3][Q1]) {
+        bool live;
+        long long bidx;
+        float sy, sz;
+        mirror_of(m, live, bidx, sy, sz);
         Unroll<0, Q1>::run([&](auto q) {
             constexpr int n2 = decltype(q)::value;
             const int slot = sm.in[t + T * n2];
@@ -956,6 +969,28 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
             x[1][n2] = make_float2(sy * v1.x, sy * v1.y);
             x[2][n2] = make_float2(sz * v2.x, sz * v2.y);
         });
+    };
+    // outputs y[t + T n2], n2 >= Q1 / 2, i.e. window positions S .. P - 1
+    auto store_outputs = [&](int m, float2 (&y)[3][Q1]) {
+        bool live;
+        long long bidx;
+        float sy, sz;
+        mirror_of(m, live, bidx, sy, sz);
+        if (!live) return;
+        const float sc = 1.f / (float)P;
+        Unroll<Q1 / 2, Q1>::run([&](auto q) {
+            constexpr int n2 = decltype(q)::value;
+            const int pos = t + T * n2;                      // >= S
+            float2* dst = a.acc + (long long)sm.out[pos - S] * 3 * a.nbins + bidx;
+            dst[0] = make_float2(sc * y[0][n2].x, sc * y[0][n2].y);
+            dst[a.nbins] = make_float2(sy * sc * y[1][n2].x, sy * sc * y[1][n2].y);
+            dst[2 * a.nbins] = make_float2(sz * sc * y[2][n2].x, sz * sc * y[2][n2].y);
+        });
+    };
+    float2 x[3][Q1];
+    if constexpr (T > 1) load_window(0, x);
+    for (int mirror = 0; mirror < 4; ++mirror) {
+        if constexpr (T == 1) load_window(mirror, x);
         Unroll<0, 3>::run([&](auto cq) { dft_ct<Q1, -1>(x[decltype(cq)::value]); });
         if constexpr (T == 1) {
             // ---- the whole product in registers: frequency w = k2
@@ -970,7 +1005,7 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
                 float2 h[6];
 #pragma unroll
                 for (int cc = 0; cc < 6; ++cc) {
-                    h[cc] = sm.H[(ws * 6 + cc) * NB + bin];
+                    h[cc] = sm.H[ws * F::HW + cc * NB + bin];
                     if (cj) h[cc].y = -h[cc].y;
                 }
                 const float2 x0 = x[0][w], x1 = x[1][w], x2 = x[2][w];
@@ -978,7 +1013,10 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
                 x[1][w] = cadd(cadd(cmul(h[3], x0), cmul(h[1], x1)), cmul(h[5], x2));
                 x[2][w] = cadd(cadd(cmul(h[4], x0), cmul(h[5], x1)), cmul(h[2], x2));
             });
+            Unroll<0, 3>::run([&](auto cq) { dft_ct<Q1, +1>(x[decltype(cq)::value]); });
+            store_outputs(mirror, x);
         } else {
+            // ---- phase A (the DFTs over n2 above), twiddles W_P^{t k2}, exchange
             Unroll<0, Q1>::run([&](auto q) {
                 constexpr int k2 = decltype(q)::value;
                 const float2 w = sm.tw[t * k2];
@@ -989,6 +1027,8 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
             });
             if (mirror == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             __syncthreads();
+            // the next mirror's window streams in while phases B and C of this one run
+            if (mirror < 3) load_window(mirror + 1, x);
             // ---- phase B: T-point DFTs over t, product, inverse, conjugate twiddles
             for (int j = 0; j < Q1 / T; ++j) {
                 const int k2 = t + T * j;
@@ -1009,7 +1049,7 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
                     float2 h[6];
 #pragma unroll
                     for (int cc = 0; cc < 6; ++cc) {
-                        h[cc] = sm.H[(ws * 6 + cc) * NB + bin];
+                        h[cc] = sm.H[ws * F::HW + cc * NB + bin];
                         if (cj) h[cc].y = -h[cc].y;
                     }
                     const float2 x0 = v[0][k1], x1 = v[1][k1], x2 = v[2][k1];
@@ -1028,27 +1068,18 @@ __global__ void __launch_bounds__(128, P == 16 ? 4 : 2) k_far_fs(FarArgs<float> 
                 });
             }
             __syncthreads();
-            // ---- phase C: gather over k2
+            // ---- phase C: gather over k2, inverse DFTs over k2, stores
+            float2 y[3][Q1];
             Unroll<0, Q1>::run([&](auto q) {
                 constexpr int k2 = decltype(q)::value;
                 const float2* src = &sm.V[k2 * F::KS + t * NB + bin];
-                x[0][k2] = src[0];
-                x[1][k2] = src[F::CS];
-                x[2][k2] = src[2 * F::CS];
+                y[0][k2] = src[0];
+                y[1][k2] = src[F::CS];
+                y[2][k2] = src[2 * F::CS];
             });
             __syncthreads();   // the next mirror's phase A overwrites V
-        }
-        Unroll<0, 3>::run([&](auto cq) { dft_ct<Q1, +1>(x[decltype(cq)::value]); });
-        if (live) {
-            const float sc = 1.f / (float)P;
-            Unroll<Q1 / 2, Q1>::run([&](auto q) {
-                constexpr int n2 = decltype(q)::value;
-                const int pos = t + T * n2;                  // >= S
-                float2* dst = a.acc + (long long)sm.out[pos - S] * 3 * a.nbins + bidx;
-                dst[0] = make_float2(sc * x[0][n2].x, sc * x[0][n2].y);
-                dst[a.nbins] = make_float2(sy * sc * x[1][n2].x, sy * sc * x[1][n2].y);
-                dst[2 * a.nbins] = make_float2(sz * sc * x[2][n2].x, sz * sc * x[2][n2].y);
-            });
+            Unroll<0, 3>::run([&](auto cq) { dft_ct<Q1, +1>(y[decltype(cq)::value]); });
+            store_outputs(mirror, y);
         }
     }
 }
