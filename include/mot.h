@@ -420,6 +420,35 @@ mot_status mot_set_profiling(mot_ctx* ctx, int enable);
 mot_status mot_get_stats(const mot_ctx* ctx, mot_stats* out);
 
 /*
+ * Probe field: the scattered field at probe voxels, for objectives such as the
+ * time-gated field energy around the scatterer.  A probe is a voxel of the grid's
+ * lattice, inside or outside the grid (lattice indices (u, v, w), any integers); its
+ * field is the tested, voxel-averaged field of Eq. E at that virtual vacuum voxel, which
+ * the march's own interaction elements give (Eq. Z; no local term in vacuum):
+ *     E^s_p(t_n) = sum_{l>=0} sum_m G_l(r_p - r_m) J_{n-l,m},
+ * and its transpose, the source of the adjoint march for an objective of E^s,
+ *     g_{k,m} = sum_{l>=0} sum_p G_l(r_p - r_m) W_{k+l,p}      (G_l is symmetric).
+ *
+ * mot_probe_setup - compute the element windows of every probe-voxel pair on the
+ *   device (the quadrature of mot_create on the distinct sorted offsets) and keep them
+ *   in the context: P x M x 6 x 8 doubles (2.7 GB for 64 probes on a 48^3 grid).
+ *   probes  host, [n_probes][3] ints (u, v, w); replaces an earlier probe set
+ *   Errors: MOT_ERR_ARG (counts, pointers, probes so far away that the offset table
+ *   exceeds 2^28 entries), MOT_ERR_OOM, MOT_ERR_CUDA.
+ * mot_probe_field - E = the probe field of the currents J.
+ *   J  [n_steps][M][3] J_1 .. J_{n_steps} (host or device);  E  [n_steps][P][3]
+ *   (host or device).  Synchronous on `stream` (or the context's stream).
+ * mot_probe_transpose - g = the transposed probe operator applied to W.
+ *   W  [n_steps][P][3] (host or device);  g  [n_steps][M][3] (host or device).
+ * FP64 throughout.  Errors: MOT_ERR_ARG (no probes, counts, NULL), MOT_ERR_OOM,
+ * MOT_ERR_CUDA.
+ */
+mot_status mot_probe_setup(mot_ctx* ctx, int n_probes, const int* probes);
+mot_status mot_probe_field(mot_ctx* ctx, int n_steps, const double* J, double* E, void* stream);
+mot_status mot_probe_transpose(mot_ctx* ctx, int n_steps, const double* W, double* g,
+                               void* stream);
+
+/*
  * mot_fma_peak - measure the current device's sustained FMA rate (no counterpart in the
  * paper: the denominator of the roofline of kernels bound by arithmetic rather than
  * memory, such as the FP64 history kernels on GPUs whose FP64 rate is a fraction of

@@ -20,24 +20,10 @@ from .kernel_table import offset_elements
 
 
 def fibonacci_probes(N, n_probes=64, radius_factor=2.0, seed=240703324):
-    """Lattice indices (u, v, w) of n_probes points of a Fibonacci lattice on the
-    sphere of radius radius_factor * N about the centre of an N^3 grid, turned by a
-    seeded random rotation; duplicates after rounding are removed."""
-    i = np.arange(n_probes) + 0.5
-    z = 1.0 - 2.0 * i / n_probes
-    phi = np.pi * (1.0 + 5.0 ** 0.5) * i
-    s = np.sqrt(1.0 - z * z)
-    pts = np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
-    q, _ = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))
-    pts = pts @ q.T * (radius_factor * N)
-    centre = N / 2.0
-    idx = np.floor(pts + centre).astype(int)            # voxel containing the point
-    out = []
-    for p in idx:
-        t = tuple(int(v) for v in p)
-        if t not in out:
-            out.append(t)
-    return np.array(out)
+    """The probe voxels of the adjoint workload (seeded input; see
+    ``workloads.fibonacci_probes``)."""
+    import workloads
+    return workloads.fibonacci_probes(N, n_probes, radius_factor, seed)
 
 
 def _elements_at(d, nlag, cache):

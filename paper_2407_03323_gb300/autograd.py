@@ -9,6 +9,12 @@ the tested plane wave of Eq. E, E_n = chi e_n, generated on the GPU from `wave`
 adjoint gradient includes that dependence.  The result is J [N][M][3] (float64, on the
 GPU), or J at the voxels `probes` only, [N][len(probes)][3].
 
+    E = probe_field(J, pctx)
+
+is the scattered field at probe voxels outside (or inside) the grid, the objective of
+field-energy problems: for O = sum over gated steps of |E|^2, O.backward() runs the
+transposed probe operator and then the adjoint march.
+
 Checkpointing (checkpoint_every = K): the forward keeps only, at every K-step
 boundary b, the block of the last min(b, ell) currents (they determine every later
 step, see mot_restart); the backward walks the segments from the last to the first,
@@ -117,6 +123,32 @@ class MarchFunction(torch.autograd.Function):
             fctx.mot = None
         g = torch.as_tensor(grad, dtype=torch.float64).reshape(fctx.eps_shape)
         return g.to(fctx.eps_device), None, None, None, None, None, None
+
+
+class ProbeFieldFunction(torch.autograd.Function):
+    """E = probe field of J (mot_probe_field); backward: the transposed probe operator
+    (mot_probe_transpose).  `pctx` is a Context of the same grid whose probes are set."""
+
+    @staticmethod
+    def forward(fctx, J, pctx):
+        J = J.detach().to(device="cuda", dtype=torch.float64).contiguous()
+        E = torch.empty((J.shape[0], pctx.n_probes, 3), dtype=torch.float64, device="cuda")
+        pctx.probe_field(J, out=E)
+        fctx.pctx = pctx
+        fctx.shape = J.shape
+        return E
+
+    @staticmethod
+    def backward(fctx, grad_E):
+        g = torch.empty(fctx.shape, dtype=torch.float64, device="cuda")
+        fctx.pctx.probe_transpose(grad_E.to(dtype=torch.float64).contiguous(), out=g)
+        return g, None
+
+
+def probe_field(J, pctx):
+    """Scattered field E [N][P][3] at the probes of `pctx` for currents J [N][M][3],
+    differentiable in J: E^s_p(t_n) = sum_l sum_m G_l(r_p - r_m) J_{n-l,m}."""
+    return ProbeFieldFunction.apply(J, pctx)
 
 
 def march(eps_r, taps, wave, n_steps, probes=None, checkpoint_every=None,

@@ -89,6 +89,8 @@ void free_all(mot_ctx* c) {
     cudaFree(c->tiles);
     cudaFree(c->diag32);
     cudaFree(c->vfac);
+    cudaFree(c->probe_tab);
+    cudaFree(c->probe_l0);
     cudaFree(c->pdsa_spec);
     cudaFree(c->pdsa_a);
     cudaFree(c->pdsa_xhat);

@@ -156,6 +156,11 @@ struct mot_ctx {
     int adj_done = 0;            //   adjoint steps done (tau)
     double* adj_gchi = nullptr;  //   dO/dchi accumulated so far (device, [M])
 
+    // probe operator (probes.cu): element windows of every probe-voxel pair
+    int n_probes = 0;
+    double* probe_tab = nullptr;   // [P][6][WIN][M]
+    int* probe_l0 = nullptr;       // [P][M]
+
     // PDSA operator A_n (pdsa.cu): kernel spectrum and diagonal of the last (n, flags)
     double* pdsa_spec = nullptr;   // [noct][6] unnormalised spectrum of sum_i c_i G_i
     double* pdsa_a = nullptr;      // [M] diagonal a_m (0 on voxels with chi = 0)
@@ -193,6 +198,8 @@ constexpr int kPwTable = 1 << 16;   // nodes of the plane-wave table of one call
 
 // quadrature.cu
 void compute_table(mot_ctx* c);
+double* quad_windows(mot_ctx* c, const std::vector<int3>& tri);
+void probe_windows(mot_ctx* c, int np, const int* probes, double* tab, int* l0);
 // spectra.cu
 void compute_spectra(mot_ctx* c);
 void spectrum_of_lag(mot_ctx* c, int l, double* host_out);

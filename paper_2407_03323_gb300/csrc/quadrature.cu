@@ -373,15 +373,13 @@ __host__ __device__ inline long long tri_before_b(long long b, long long L3) {
     return b <= L3 ? b * (b + 1) / 2 : L3 * (L3 + 1) / 2 + (b - L3) * L3;
 }
 
-// octant assembly: G_l^{ab}(d) = K^face^{ab} - delta_ab K^vol, windowed in lag
-__global__ void assemble_kernel(const double* __restrict__ res, int U, int V, int W,
-                                const long long* __restrict__ off_a, int L3,
-                                int* __restrict__ tab_l0, double* __restrict__ tab) {
-    const long long oct = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long n = (long long)U * V * W;
-    if (oct >= n) return;
-    const int dx = (int)(oct % U), dy = (int)((oct / U) % V), dz = (int)(oct / ((long long)U * V));
-    int d[3] = {dx, dy, dz};
+// G_l^{ab}(d) = K^face^{ab} - delta_ab K^vol for lags l0 .. l0 + WIN - 1 of the offset
+// d >= 0 (componentwise) from the three axis passes `res` of its sorted triple: the face
+// matrix of the sorted frame, permuted back to d's axes.  Writes the six components
+// (xx, yy, zz, xy, xz, yz) at dst[c * cstride + i * lstride] and returns l0.
+__device__ inline int assemble_window(const double* __restrict__ res, const int d[3],
+                                      double* __restrict__ dst, long long cstride,
+                                      long long lstride) {
     // sort descending with the permutation p: d[i] = key[p[i]]
     int order[3] = {0, 1, 2};
     for (int i = 0; i < 3; ++i)
@@ -390,11 +388,9 @@ __global__ void assemble_kernel(const double* __restrict__ res, int U, int V, in
     int key[3] = {d[order[0]], d[order[1]], d[order[2]]};
     int p[3];
     for (int k = 0; k < 3; ++k) p[order[k]] = k;
-    const long long a = key[0], b = key[1], c = key[2];
-    const long long t = off_a[a] + tri_before_b(b, L3) + c;
-    const double* r0 = res + (t * 3 + 0) * 3 * mot::WIN;   // axis z pass
-    const double* r1 = res + (t * 3 + 1) * 3 * mot::WIN;   // axis x pass
-    const double* r2 = res + (t * 3 + 2) * 3 * mot::WIN;   // axis y pass
+    const double* r0 = res;                       // axis z pass
+    const double* r1 = res + 3 * mot::WIN;        // axis x pass
+    const double* r2 = res + 6 * mot::WIN;        // axis y pass
     // face matrix in the sorted frame
     const double* F[3][3];
     F[2][2] = r0 + mot::WIN; F[0][1] = r0 + 2 * mot::WIN; F[1][0] = F[0][1];
@@ -404,19 +400,156 @@ __global__ void assemble_kernel(const double* __restrict__ res, int U, int V, in
     const double rmin = sqrt((double)(max(key[0] - 1, 0) * max(key[0] - 1, 0) +
                                       max(key[1] - 1, 0) * max(key[1] - 1, 0) +
                                       max(key[2] - 1, 0) * max(key[2] - 1, 0)));
-    tab_l0[oct] = (int)floor(rmin);
     const int comp_a[6] = {0, 1, 2, 0, 0, 1}, comp_b[6] = {0, 1, 2, 1, 2, 2};
     for (int cc = 0; cc < 6; ++cc) {
         const int aa = comp_a[cc], bb = comp_b[cc];
         const double* f = F[p[aa]][p[bb]];
         for (int i = 0; i < mot::WIN; ++i)
-            tab[(oct * 6 + cc) * mot::WIN + i] = f[i] - (aa == bb ? vol[i] : 0.0);
+            dst[cc * cstride + i * lstride] = f[i] - (aa == bb ? vol[i] : 0.0);
     }
+    return (int)floor(rmin);
+}
+
+// octant assembly: G_l^{ab}(d) = K^face^{ab} - delta_ab K^vol, windowed in lag
+__global__ void assemble_kernel(const double* __restrict__ res, int U, int V, int W,
+                                const long long* __restrict__ off_a, int L3,
+                                int* __restrict__ tab_l0, double* __restrict__ tab) {
+    const long long oct = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)U * V * W;
+    if (oct >= n) return;
+    const int d[3] = {(int)(oct % U), (int)((oct / U) % V), (int)(oct / ((long long)U * V))};
+    int key[3] = {d[0], d[1], d[2]};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (key[j] > key[i]) { int tmp = key[i]; key[i] = key[j]; key[j] = tmp; }
+    const long long t = off_a[key[0]] + tri_before_b(key[1], L3) + key[2];
+    tab_l0[oct] = assemble_window(res + t * 9 * mot::WIN, d, tab + oct * 6 * mot::WIN, mot::WIN, 1);
+}
+
+// Probe windows: for probe p (lattice indices, outside the grid or not) and voxel m,
+// G_l(r_p - r_m) for lags l0 .. l0 + WIN - 1 with the parity signs of the full offset
+// (diagonal components even in every d_i, the (a, b) component odd in d_a and in d_b,
+// zero when either is 0).  Layout tab[p][c][i][m] (voxels fastest), l0[p][m].
+__global__ void assemble_probe_kernel(const double* __restrict__ res, const int* __restrict__ kidx,
+                                      int A, const int3* __restrict__ probes, int np, int U, int V,
+                                      int W, int* __restrict__ l0, double* __restrict__ tab) {
+    const long long M = (long long)U * V * W;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * np) return;
+    const int p = (int)(i / M);
+    const long long m = i % M;
+    const int3 q = probes[p];
+    const int d[3] = {q.x - (int)(m % U), q.y - (int)((m / U) % V), q.z - (int)(m / ((long long)U * V))};
+    const int ad[3] = {abs(d[0]), abs(d[1]), abs(d[2])};
+    int key[3] = {ad[0], ad[1], ad[2]};
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            if (key[b] > key[a]) { int tmp = key[a]; key[a] = key[b]; key[b] = tmp; }
+    const long long t = kidx[((long long)key[0] * (A + 1) + key[1]) * (A + 1) + key[2]];
+    double w[6 * mot::WIN];
+    const int lo = assemble_window(res + t * 9 * mot::WIN, ad, w, mot::WIN, 1);
+    const double sx = (d[0] > 0) - (d[0] < 0), sy = (d[1] > 0) - (d[1] < 0),
+                 sz = (d[2] > 0) - (d[2] < 0);
+    const double sgn[6] = {1.0, 1.0, 1.0, sx * sy, sx * sz, sy * sz};
+    for (int c = 0; c < 6; ++c)
+        for (int k = 0; k < mot::WIN; ++k)
+            tab[(((long long)p * 6 + c) * mot::WIN + k) * M + m] = w[c * mot::WIN + k] * sgn[c];
+    l0[(long long)p * M + m] = lo;
 }
 
 }  // namespace
 
 namespace mot {
+
+void probe_windows(mot_ctx* c, int np, const int* probes, double* tab, int* l0) {
+    const int N[3] = {c->U, c->V, c->W};
+    // largest offset component over all probe-voxel pairs
+    int A = 0;
+    for (int p = 0; p < np; ++p)
+        for (int a = 0; a < 3; ++a) {
+            A = std::max(A, std::abs(probes[3 * p + a]));
+            A = std::max(A, std::abs(probes[3 * p + a] - (N[a] - 1)));
+        }
+    if ((long long)(A + 1) * (A + 1) * (A + 1) > (1LL << 28))
+        throw MotError{MOT_ERR_ARG, "probes too far from the grid (offset table over 2^28 entries)"};
+    const long long A1 = A + 1;
+    std::vector<int> kidx((size_t)(A1 * A1 * A1), -1);
+    std::vector<int3> tri;
+    for (int p = 0; p < np; ++p)
+        for (int w = 0; w < c->W; ++w)
+            for (int v = 0; v < c->V; ++v)
+                for (int u = 0; u < c->U; ++u) {
+                    int k[3] = {std::abs(probes[3 * p] - u), std::abs(probes[3 * p + 1] - v),
+                                std::abs(probes[3 * p + 2] - w)};
+                    std::sort(k, k + 3, [](int x, int y) { return x > y; });
+                    int& slot = kidx[(size_t)((k[0] * A1 + k[1]) * A1 + k[2])];
+                    if (slot < 0) {
+                        slot = (int)tri.size();
+                        tri.push_back(make_int3(k[0], k[1], k[2]));
+                    }
+                }
+    double* res = quad_windows(c, tri);
+    int* dk = nullptr;
+    int3* dp = nullptr;
+    try {
+        MOT_CUDA_TRY(cudaMalloc(&dk, sizeof(int) * kidx.size()));
+        MOT_CUDA_TRY(cudaMalloc(&dp, sizeof(int3) * np));
+        MOT_CUDA_TRY(cudaMemcpyAsync(dk, kidx.data(), sizeof(int) * kidx.size(),
+                                     cudaMemcpyHostToDevice, c->stream));
+        MOT_CUDA_TRY(cudaMemcpyAsync(dp, probes, sizeof(int3) * np, cudaMemcpyHostToDevice,
+                                     c->stream));
+        const long long tot = c->M * np;
+        assemble_probe_kernel<<<(int)((tot + 255) / 256), 256, 0, c->stream>>>(
+            res, dk, A, dp, np, c->U, c->V, c->W, l0, tab);
+        MOT_LAUNCH_CHECK();
+        MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    } catch (...) {
+        cudaFree(res);
+        cudaFree(dk);
+        cudaFree(dp);
+        throw;
+    }
+    cudaFree(res);
+    cudaFree(dk);
+    cudaFree(dp);
+}
+
+
+// Element windows of arbitrary sorted triples a >= b >= c >= 0 (the three axis passes,
+// [t][3][3][WIN], device memory owned by the caller); the rules are in constant memory
+// after compute_table has run on this device.
+double* quad_windows(mot_ctx* c, const std::vector<int3>& tri) {
+    const int nt = (int)tri.size();
+    int3* dtri = nullptr;
+    double* dres = nullptr;
+    int* derr = nullptr;
+    try {
+        MOT_CUDA_TRY(cudaMalloc(&dtri, sizeof(int3) * std::max(nt, 1)));
+        MOT_CUDA_TRY(cudaMalloc(&dres, sizeof(double) * (size_t)std::max(nt, 1) * 9 * WIN));
+        MOT_CUDA_TRY(cudaMalloc(&derr, sizeof(int)));
+        MOT_CUDA_TRY(cudaMemsetAsync(derr, 0, sizeof(int), c->stream));
+        if (nt > 0) {
+            MOT_CUDA_TRY(cudaMemcpyAsync(dtri, tri.data(), sizeof(int3) * nt,
+                                         cudaMemcpyHostToDevice, c->stream));
+            const long long jobs = 3LL * nt;
+            const int blocks = (int)((jobs + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+            quad_kernel<<<blocks, 32 * WARPS_PER_BLOCK, 0, c->stream>>>(dtri, nt, dres, derr);
+            MOT_LAUNCH_CHECK();
+        }
+        int herr = 0;
+        MOT_CUDA_TRY(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (herr) throw MotError{MOT_ERR_CUDA, "element quadrature: lag window overflow"};
+    } catch (...) {
+        cudaFree(dtri);
+        cudaFree(dres);
+        cudaFree(derr);
+        throw;
+    }
+    cudaFree(dtri);
+    cudaFree(derr);
+    return dres;
+}
 
 void compute_table(mot_ctx* c) {
     {

@@ -33,7 +33,8 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
-           "mot_frequency_response", "mot_fma_peak", "mot_last_error"]
+           "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
+           "mot_probe_transpose", "mot_last_error"]
 MOT_PDSA_FP32_SPECTRUM = 1
 MOT_PDSA_FULL_REORTH = 2
 
@@ -94,6 +95,9 @@ def load_library(path=LIB_PATH):
     lib.mot_fir_magnitude.argtypes = [P, I, I, P, P]
     lib.mot_frequency_response.argtypes = [I, I, P, D, D, P, D, D, I, P, P, P]
     lib.mot_fma_peak.argtypes = [I, I, P, P]
+    lib.mot_probe_setup.argtypes = [P, I, P]
+    lib.mot_probe_field.argtypes = [P, I, P, P, P]
+    lib.mot_probe_transpose.argtypes = [P, I, P, P, P]
     lib.mot_last_error.argtypes = [P]
     lib.mot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -435,6 +439,41 @@ class Context:
                                                ext.ctypes.data))
         return {"ritz": ritz[:info[0]].copy(), "theta_min": ext[0], "resid_min": ext[1],
                 "theta_max": ext[2], "resid_max": ext[3], "steps": info[1]}
+
+    # ---------------------------------------------------------------- probe field
+    def probe_setup(self, probes):
+        """Element windows of every probe-voxel pair (mot_probe_setup); probes are
+        lattice indices (u, v, w), [n][3] ints, inside or outside the grid."""
+        q = np.ascontiguousarray(np.asarray(probes, dtype=np.int32).reshape(-1, 3))
+        self._check(self._lib.mot_probe_setup(self._h, q.shape[0], q.ctypes.data))
+        self.n_probes = q.shape[0]
+
+    def probe_field(self, J, out=None, stream=None):
+        """Scattered field E[n][p][3] at the probes for currents J[n][M][3]
+        (mot_probe_field); numpy arrays or CUDA tensors."""
+        if isinstance(J, np.ndarray):
+            J = np.ascontiguousarray(J, dtype=np.float64)
+        if not _dtype_ok(J):
+            raise TypeError("J must be float64")
+        n = J.shape[0]
+        if out is None:
+            out = np.zeros((n, self.n_probes, 3))
+        self._check(self._lib.mot_probe_field(self._h, n, _ptr(J), _ptr(out), _stream(stream)))
+        return out
+
+    def probe_transpose(self, W, out=None, stream=None):
+        """Transposed probe operator g[k][M][3] applied to W[n][p][3]
+        (mot_probe_transpose); numpy arrays or CUDA tensors."""
+        if isinstance(W, np.ndarray):
+            W = np.ascontiguousarray(W, dtype=np.float64)
+        if not _dtype_ok(W):
+            raise TypeError("W must be float64")
+        n = W.shape[0]
+        if out is None:
+            out = np.zeros((n, self.M, 3))
+        self._check(self._lib.mot_probe_transpose(self._h, n, _ptr(W), _ptr(out),
+                                                  _stream(stream)))
+        return out
 
     @property
     def levels(self):

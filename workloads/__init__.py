@@ -75,6 +75,27 @@ def pulse(N, eps_for_fc, k_hat=(0.0, 0.0, 1.0), p_hat=(1.0, 0.0, 0.0), frac_bw=0
     return {"k_hat": k, "p_hat": p, "f_c": fc, "sigma_t": sigma_t, "t0": t0}
 
 
+def fibonacci_probes(N, n_probes=64, radius_factor=2.0, seed=MASTER_SEED + 1):
+    """Lattice indices (u, v, w) of the probes of the adjoint workload: n_probes points
+    of a Fibonacci lattice on the sphere of radius radius_factor * N about the centre of
+    an N^3 grid, turned by a seeded random rotation, each rounded down to the voxel that
+    contains it; duplicates after rounding are removed (first occurrence kept)."""
+    i = np.arange(n_probes) + 0.5
+    z = 1.0 - 2.0 * i / n_probes
+    phi = np.pi * (1.0 + 5.0 ** 0.5) * i
+    s = np.sqrt(1.0 - z * z)
+    pts = np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=1)
+    q, _ = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))
+    pts = pts @ q.T * (radius_factor * N)
+    idx = np.floor(pts + N / 2.0).astype(int)
+    out = []
+    for p in idx:
+        t = tuple(int(v) for v in p)
+        if t not in out:
+            out.append(t)
+    return np.array(out)
+
+
 def random_directions(n, seed):
     """n seeded propagation directions uniform on S^2, each with a random orthogonal
     polarisation."""
