@@ -8,6 +8,7 @@ application, march step and transform runs in the library's kernels).
     python -m paper_2407_03323_gb300.diagnostics sphere100
     python -m paper_2407_03323_gb300.diagnostics response
     python -m paper_2407_03323_gb300.diagnostics adjoint
+    python -m paper_2407_03323_gb300.diagnostics stability
 
 * pdsa        smallest eigenvalue of A_n = diag(1/chi) D_n / C(ell, n) (Eq. Dn) on
               cubes of growing side: Lanczos Ritz values (a negative one certifies that
@@ -28,6 +29,8 @@ application, march step and transform runs in the library's kernels).
 * adjoint     gradient of the gated scattered-field energy at 64 probes around a
               heterogeneous 48^3 block (2048 steps, checkpoints every 64) against central
               differences at 32 voxels.
+* stability   the 104^3 eps_r = 12 sphere marched 40,960 steps (10x the workload) in
+              FP32-history: maxima of ||J_n|| over every 2048 steps.
 
 Geometry as in the paper: the 0.2 m cube discretised by N^3 voxels with c0 dt = h,
 probe r = (0.025, 0.075, 0.025) m -> voxel (N/8, 3N/8, N/8), the x-polarised Gaussian
@@ -324,10 +327,47 @@ def adjoint_probes(N=48, steps=2048, n_probes=64, checkpoint=64, n_fd=32, h=1e-4
             "gradient_s": t_grad, "fd_s_per_march": t_fd / (2 * n_fd), **opts}
 
 
+def stability(config="sphere104", steps=40960, window=2048, chunk=256,
+              precision="fp32_history", scheme="blocked", block=8):
+    """Late-time stability of a long march (Secs. 5.2, 6): the workload's pulse, then
+    E = 0; ||J_n|| of every step (summed on the device), reported as the maximum over
+    each window of `window` steps.  The FIR-regularised march is stable when these
+    maxima never grow after the pulse."""
+    import torch
+    cfg = wl.config(config)
+    eps, taps, p = cfg["eps_r"], cfg["taps"], cfg["pulse"]
+    ctx = _mot.Context(eps, taps, precision=precision, scheme=scheme, block=block)
+    M = ctx.M
+    buf = torch.empty((chunk, M, 3), dtype=torch.float64, device="cuda")
+    E = torch.empty((chunk, M, 3), dtype=torch.float64, device="cuda")
+    norms = []
+    t = time.time()
+    for n0 in range(1, steps + 1, chunk):
+        k = min(chunk, steps + 1 - n0)
+        if n0 <= 2 * p["t0"]:                     # the pulse; E = 0 once it has passed
+            ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"], n0, k,
+                           out=E[:k])
+            ctx.set_excitation(E[:k])
+        ctx.march(k, out=buf[:k])
+        norms.append(torch.linalg.vector_norm(buf[:k].reshape(k, -1), dim=1).cpu().numpy())
+    torch.cuda.synchronize()
+    wall = time.time() - t
+    norms = np.concatenate(norms)
+    ctx.close()
+    wins = [float(norms[i:i + window].max()) for i in range(0, steps, window)]
+    after = wins[1:]
+    return {"config": config, "precision": precision, "scheme": scheme, "steps": steps,
+            "finite": bool(np.all(np.isfinite(norms))), "peak": float(norms.max()),
+            "window": window, "window_max": wins,
+            "never_grows_after_first": bool(all(b <= a for a, b in zip(after, after[1:]))),
+            "last_over_peak": wins[-1] / float(norms.max()), "wall_s": wall,
+            "ms_per_step": 1e3 * wall / steps}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("what", choices=["pdsa", "truncation", "fir", "sphere100", "response",
-                                     "adjoint"])
+                                     "adjoint", "stability"])
     ap.add_argument("--sides", default="4,6,8,10,12,14,16,20,24,32")
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--k", type=int, default=20000)
@@ -353,6 +393,9 @@ def main(argv=None):
         out = sphere100(N=a.N or 105, eps_r=a.eps or 100.0, steps=a.steps or 2000)
     elif a.what == "adjoint":
         out = adjoint_probes(N=a.N or 48, steps=a.steps or 2048)
+    elif a.what == "stability":
+        out = stability(steps=a.steps or 40960, precision=a.precision
+                        if a.precision != "fp64" else "fp32_history")
     else:
         out = response(N=a.N or 20, eps_r=a.eps or 12.0, steps=a.steps)
     print(json.dumps(out, indent=1, default=float))
