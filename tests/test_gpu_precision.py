@@ -6,8 +6,10 @@ FIR-regularised scheme is stable; the FP32 history must not undo that).
 Bounds: one FP32 FFT convolution carries ~2e-7 relative error, and the march amplifies
 perturbations of its history by ~1e3 over 2048 steps on these high-Q eps_r = 12
 spheres (the FP64 direct-sum and blocked schemes, which differ only in rounding order,
-end up 1e-13 apart).  The FP32-history deviation is therefore ~3e-5 (32^3, 2048 steps)
-and ~1e-5 (104^3, 640 steps); the bounds below leave a margin of about 2."""
+end up 1e-13 apart).  The FP32-history deviation is therefore ~3e-5 on the 32^3 sphere
+over 2048 steps (bound 5e-5: the 1e-5 target is not met there; nine tenths of it come
+from the FP32 transforms and storage of J's spectra) and 8e-6 at 104^3 over 640 steps
+(bound 1e-5, the target)."""
 import os
 
 import numpy as np
@@ -88,4 +90,4 @@ def test_sphere104_fp32_vs_fp64(mot):
     rel = np.sqrt(num / den)
     print("\nsphere104: FP32-history vs FP64 rel L2 over %d steps = %.3e" % (steps, rel))
     assert den > 0
-    assert rel < 3e-5
+    assert rel < 1e-5                  # the FP32-history target
