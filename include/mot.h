@@ -462,6 +462,24 @@ mot_status mot_probe_transpose(mot_ctx* ctx, int n_steps, const double* W, doubl
  */
 mot_status mot_fma_peak(int fp64, int iters, float* ms, double* flops);
 
+/*
+ * mot_barrier_check - exercise the bounded wait of the grid barrier that the solve
+ * kernel (the CG of Eq. MOTInversion) uses between its passes (no counterpart in the
+ * paper: a failure guard).  One cooperative launch of n_blocks blocks on the current
+ * device passes `rounds` barriers; block `absent` (0 <= absent < n_blocks; -1: none)
+ * returns without arriving, so the other blocks' wait runs out after budget_s seconds
+ * of SM clock and the launch ends with a timeout instead of hanging.  Synchronous.
+ *  passed         receives the number of blocks that passed every round
+ *  timeout_round  receives the round (1-based) at which the wait ran out, 0 if none
+ * Returns MOT_OK, MOT_ERR_TIMEOUT (the wait ran out), MOT_ERR_ARG (n_blocks above what
+ * can be resident at once, rounds outside 1..2^20, budget_s outside (0, 10], NULL
+ * outputs), MOT_ERR_OOM, MOT_ERR_CUDA.  The solve reports the same timeout of one of
+ * its barriers (2 s budget) as MOT_ERR_TIMEOUT from mot_march / mot_adjoint_run, with
+ * the step in mot_last_error, and the context becomes unusable (MOT_ERR_STATE).
+ */
+mot_status mot_barrier_check(int n_blocks, int rounds, int absent, double budget_s,
+                             int* passed, int* timeout_round);
+
 /* Last error message of ctx, or of the last failed mot_create when ctx is NULL. */
 const char* mot_last_error(const mot_ctx* ctx);
 

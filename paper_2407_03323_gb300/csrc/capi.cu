@@ -286,6 +286,10 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
                             if (any) tl.push_back(x0 | (y0 << 10) | (z0 << 20));
                         }
                 c->ntiles = (int)tl.size();
+                // one block per tile at most: the tiled passes give a block one tile at
+                // a time, so further blocks would only wait at the grid barriers (and
+                // keep SMs from concurrent solves of other contexts)
+                c->cg_blocks = std::min(c->cg_blocks, std::max(c->ntiles, 1));
                 MOT_CUDA_TRY(cudaMalloc(&c->tiles, sizeof(int) * std::max<size_t>(tl.size(), 1)));
                 if (!tl.empty())
                     MOT_CUDA_TRY(cudaMemcpy(c->tiles, tl.data(), sizeof(int) * tl.size(),
@@ -317,8 +321,8 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         }
         MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
         if (c->nact) mot::chebyshev_setup(c);
-        MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
-        MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
+        MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * mot::kStatusWords));
+        MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * mot::kStatusWords));
         MOT_CUDA_TRY(cudaMalloc(&c->pw_tab, sizeof(double) * mot::kPwTable));
         reset_state(c, c->stream);
         MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -372,7 +376,7 @@ mot_status mot_create_shared(mot_ctx* src, mot_ctx** out) {
         c->lev_fft[k] = src->lev_fft[k]; c->lev_acc[k] = src->lev_acc[k];
     }
     c->smax = src->smax;
-    c->nsm = src->nsm; c->cg_blocks = src->cg_blocks;
+    c->nsm = src->nsm; c->cg_blocks = src->cg_blocks; c->bar_budget = src->bar_budget;
     c->device = src->device;
     c->shared_src = src;
     src->n_shared += 1;
@@ -394,8 +398,8 @@ mot_status mot_create_shared(mot_ctx* src, mot_ctx** out) {
                                     cudaMemcpyDeviceToDevice));
         }
         MOT_CUDA_TRY(cudaMalloc(&c->red, sizeof(double) * 3 * std::max(c->cg_blocks, 1)));
-        MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * 4));
-        MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * 4));
+        MOT_CUDA_TRY(cudaMalloc(&c->dstatus, sizeof(int) * mot::kStatusWords));
+        MOT_CUDA_TRY(cudaMemset(c->dstatus, 0, sizeof(int) * mot::kStatusWords));
         MOT_CUDA_TRY(cudaMalloc(&c->pw_tab, sizeof(double) * mot::kPwTable));
         reset_state(c, c->stream);
         MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -515,7 +519,7 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
             }
         }
         int waited_chunk = -1;
-        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
+        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * mot::kStatusWords, s));
         if (c->profiling) ensure_events(c, 6 * (size_t)n_steps);
         for (int i = 0; i < n_steps; ++i) {
             const int n = c->n_done + 1 + i;
@@ -596,6 +600,15 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
             }
             if (std::isfinite(v)) c->peak_norm = std::max(c->peak_norm, v);
             c->last_norm = v;
+        }
+        if (hs[1] & 4) {   // a grid barrier of the solve timed out: J from that step on is void
+            result = MOT_ERR_TIMEOUT;
+            c->fail_step = hs[2];
+            c->broken = true;
+            char b[160];
+            snprintf(b, sizeof b, "timeout: a grid barrier of the solve at step %d waited longer "
+                     "than %.1f s", hs[2], mot::kBarrierBudgetS);
+            c->err = b;
         }
         if (result == MOT_OK && (hs[1] & 2)) {   // non-finite solve (the norm check above
             result = MOT_ERR_UNSTABLE;             // catches it too; kept for clarity)
@@ -722,7 +735,7 @@ mot_status mot_adjoint_begin(mot_ctx* c, int n_total, void* stream) {
         c->adjoint = true;
         c->adj_total = n_total;
         c->adj_done = 0;
-        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * 4, s));
+        MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * mot::kStatusWords, s));
         MOT_CUDA_TRY(cudaStreamSynchronize(s));
     });
     if (st != MOT_OK) adjoint_release(c);
@@ -780,7 +793,11 @@ mot_status mot_adjoint_run(mot_ctx* c, int n_count, const double* J_win, int win
                                          cudaMemcpyDeviceToHost, s));
         MOT_CUDA_TRY(cudaStreamSynchronize(s));
         c->adj_done += n_count;
-        if (hs[1] & 2) {
+        if (hs[1] & 4) {
+            result = MOT_ERR_TIMEOUT;
+            c->broken = true;
+            c->err = "adjoint: a grid barrier of the solve timed out";
+        } else if (hs[1] & 2) {
             result = MOT_ERR_UNSTABLE;
             c->err = "adjoint: NaN or Inf in lambda";
         } else if (hs[1] & 1) {

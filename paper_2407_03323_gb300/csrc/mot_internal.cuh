@@ -112,7 +112,10 @@ struct mot_ctx {
     float cheb_inv_theta = 0.f;
     float cheb_c1[64] = {0}, cheb_c2[64] = {0};
     double* red = nullptr;       // reduction scratch
-    int* dstatus = nullptr;      // [0] cg iterations of last step, [1] flags
+    int* dstatus = nullptr;      // [0] cg iterations of last step, [1] flags, [2] first bad
+                                 // step, [3] total iterations, [4..6] the solve kernel's
+                                 // grid barrier (arrivals, generation, abort)
+    long long bar_budget = 0;    // longest barrier wait of the solve kernel, SM clock cycles
     double* norms = nullptr;     // per-step ||J_n||^2 of the current call
     int norms_cap = 0;
     double* outbuf = nullptr;    // kOutSlots steps of AoS J for host outputs (a ring)
@@ -195,6 +198,8 @@ namespace mot {
 
 constexpr int WIN = 8;  // lag window per octant offset of the interaction table
 constexpr int kPwTable = 1 << 16;   // nodes of the plane-wave table of one call
+constexpr int kStatusWords = 8;     // device status words of a context (dstatus)
+constexpr double kBarrierBudgetS = 2.0;   // longest wait at a grid barrier of the solve
 
 // quadrature.cu
 void compute_table(mot_ctx* c);

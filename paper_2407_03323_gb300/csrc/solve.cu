@@ -10,17 +10,14 @@
 // with conjugate gradients on A = diag((T(0)/eps + delta_0)/chi) - G_0 and b = rhs/chi.
 // Voxels with eps = 1 (chi = 0) carry J = rhs / (T(0) + delta_0), which is zero for
 // the zero initial state.  The CG runs as one cooperative kernel with grid-wide
-// barriers; it stops at ||r|| <= tol ||b|| or after max_iter iterations.
+// barriers (bounded waits: a barrier that is not reached in time ends the kernel with
+// a timeout flag); it stops at ||r|| <= tol ||b|| or after max_iter iterations.
 #include "mot_internal.cuh"
 
 #include <type_traits>
 
-#include <cooperative_groups.h>
-
 #include <algorithm>
 #include <cmath>
-
-namespace cg = cooperative_groups;
 
 namespace {
 
@@ -138,6 +135,8 @@ struct CGArgs {
     int max_outer;
     int step;             // time index n (for the status record)
     int* status;          // [0] inner its, [1] flags, [2] first bad step, [3] total its
+    unsigned* bar;        // grid barrier: [0] arrivals, [1] generation, [2] abort
+    long long bar_budget; // longest wait at one barrier, SM clock cycles
     double* norm2;        // ||x||^2 output
 };
 
@@ -520,6 +519,67 @@ __device__ __forceinline__ double grid_total(const double* red, int nb) {
     return r;
 }
 
+// Grid-wide barrier of a cooperative launch (every block resident) with a bounded wait.
+// After a block-level barrier, thread 0 of each block publishes the block's writes
+// (fence), arrives on a counter and, unless it is the last to arrive, waits for the
+// generation word to change; the last block resets the counter and advances the
+// generation.  A wait longer than `budget` SM clock cycles (a block that never
+// arrives) sets the abort word and the timeout flag (4) in status[1] with the step in
+// status[2]; blocks that see the abort word leave at once.  Returns false when the
+// caller must return: the kernel ends without touching the solution any further.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ bool grid_barrier(unsigned* bar, long long budget, int* status, int step) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = ld_acquire_gpu(bar + 2) == 0;
+        if (ok) {
+            const unsigned gen = ld_acquire_gpu(bar + 1);
+            __threadfence();
+            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+                bar[0] = 0u;
+                st_release_gpu(bar + 1, gen + 1u);
+            } else {
+                const long long t0 = clock64();
+                while (ld_acquire_gpu(bar + 1) == gen) {
+                    if (ld_acquire_gpu(bar + 2) != 0u) { ok = 0; break; }
+                    if (clock64() - t0 > budget) {
+                        atomicExch(bar + 2, 1u);
+                        atomicOr(status + 1, 4);
+                        atomicCAS(status + 2, 0, step);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Check of the barrier's bounded wait: every block passes `rounds` barriers, except the
+// block `absent` (>= 0), which returns at once; the others' wait then runs out.
+// w[1] flags, w[2] the round of a timeout, w[4..6] the barrier, w[7] blocks that
+// passed every round.
+__global__ void __launch_bounds__(NT) k_barrier_check(int* w, long long budget, int rounds,
+                                                      int absent) {
+    if ((int)blockIdx.x == absent) return;
+    for (int r = 1; r <= rounds; ++r)
+        if (!grid_barrier(reinterpret_cast<unsigned*>(w + 4), budget, w, r)) return;
+    if (threadIdx.x == 0) atomicAdd(w + 7, 1);
+}
+
 // Mixed-precision iterative refinement: FP64 residual r = b - A x, FP32 conjugate
 // gradients for A e = r / ||r|| to a relative ~1e-5, x += ||r|| e; repeat until the
 // FP64 residual meets tol ||b||.  All blocks take identical decisions because every
@@ -528,7 +588,7 @@ __device__ __forceinline__ double grid_total(const double* red, int nb) {
 // mode); x is split at entry, corrected in pairs and merged back to FP64 at exit.
 template <bool DF>
 __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) {
-    cg::grid_group grid = cg::this_grid();
+    auto gsync = [&] { return grid_barrier(a.bar, a.bar_budget, a.status, a.step); };
     __shared__ float4 sd[2][TH * TH * TH];        // tile halos of the tiled passes
     const long long M = a.M;
     const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -555,7 +615,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
             a.bh[m] = h;
             a.bl[m] = l;
         }
-        grid.sync();
+        if (!gsync()) return;
     }
     while (true) {
         // ---- residual (FP64, or double-float rounded to FP32)
@@ -579,11 +639,11 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         }
         block_sum2(rr_p, bb_p);
         if (threadIdx.x == 0) { red0[blockIdx.x] = rr_p; red1[blockIdx.x] = bb_p; }
-        grid.sync();
+        if (!gsync()) return;
         rr = grid_total(red0, nb);
         if (first) bb = grid_total(red1, nb);
         first = false;
-        grid.sync();   // all blocks have read red0/red1
+        if (!gsync()) return;   // all blocks have read red0/red1
         if (!(rr <= 1e300) || !(bb <= 1e300)) {
             // NaN or Inf in the right-hand side (or the start): no iteration can help;
             // J_n is returned as NaN so that the monitor and the caller see it
@@ -630,12 +690,12 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
             a.p[m] = make_float4(rv.x * a.inv_theta, rv.y * a.inv_theta, rv.z * a.inv_theta, 0.f);
             a.e[m] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        grid.sync();
+        if (!gsync()) return;
         float4* dk = a.p;
         float4* dn = a.q;
         for (int k = 0; k < n_it; ++k) {
             cheb_pass_tiled(a, dk, dn, a.c1[k], a.c2[k], sd);
-            grid.sync();
+            if (!gsync()) return;
             float4* t = dk; dk = dn; dn = t;
         }
         its += n_it;
@@ -664,7 +724,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
                 a.x[2 * M + m] += back * (double)ev.z;
             }
         }
-        grid.sync();
+        if (!gsync()) return;
         ++outer;
     }
     if (DF && !zeroed && !nonfinite) {   // x = hi + lo back in FP64
@@ -675,17 +735,18 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
             a.x[M + m] = (double)h.y + (double)l.y;
             a.x[2 * M + m] = (double)h.z + (double)l.z;
         }
-        grid.sync();
+        if (!gsync()) return;
     }
-    if (zeroed || nonfinite) grid.sync();   // x written above is read by other blocks below
+    // x written above is read by other blocks below
+    if ((zeroed || nonfinite) && !gsync()) return;
     // norm of the solution (all voxels, active and not)
     double xx = 0.0, dummy = 0.0;
     for (long long m = t0; m < M; m += gs)
         for (int c = 0; c < 3; ++c) xx += a.x[c * M + m] * a.x[c * M + m];
     block_sum2(xx, dummy);
-    grid.sync();
+    if (!gsync()) return;
     if (threadIdx.x == 0) red0[blockIdx.x] = xx;
-    grid.sync();
+    if (!gsync()) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const double nx = grid_total(red0, nb);
         *a.norm2 = nx;
@@ -927,6 +988,9 @@ void stencil_setup(mot_ctx* c) {
     if (per_sm < 1) throw MotError{MOT_ERR_CUDA, "CG kernel cannot be made resident"};
     const long long need = (c->M + NT - 1) / NT;
     c->cg_blocks = (int)std::min<long long>((long long)per_sm * c->nsm, std::max<long long>(need, 1));
+    int khz = 0;
+    MOT_CUDA_TRY(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, c->device));
+    c->bar_budget = (long long)(kBarrierBudgetS * 1e3 * std::max(khz, 1000000));
 }
 
 namespace {
@@ -1107,6 +1171,8 @@ CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
     a.max_outer = 12;
     a.step = n;
     a.status = c->dstatus;
+    a.bar = reinterpret_cast<unsigned*>(c->dstatus + 4);
+    a.bar_budget = c->bar_budget;
     a.norm2 = norm2_out;
     return a;
 }
@@ -1179,3 +1245,40 @@ void write_aos(mot_ctx* c, int n, double* out_dev, cudaStream_t s) {
 }
 
 }  // namespace mot
+
+extern "C" mot_status mot_barrier_check(int n_blocks, int rounds, int absent, double budget_s,
+                                        int* passed, int* timeout_round) {
+    if (!passed || !timeout_round || rounds < 1 || rounds > (1 << 20) || absent < -1 ||
+        absent >= n_blocks || !(budget_s > 0.0 && budget_s <= 10.0))
+        return MOT_ERR_ARG;
+    int dev = 0, nsm = 0, per_sm = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_barrier_check, NT, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return MOT_ERR_CUDA;
+    }
+    if (n_blocks < 1 || n_blocks > per_sm * nsm) return MOT_ERR_ARG;   // must be co-resident
+    int* w = nullptr;
+    if (cudaMalloc(&w, sizeof(int) * 8) != cudaSuccess) {
+        cudaGetLastError();
+        return MOT_ERR_OOM;
+    }
+    long long budget = (long long)(budget_s * 1e3 * std::max(khz, 1000000));
+    void* args[] = {&w, &budget, &rounds, &absent};
+    int h[8] = {0};
+    cudaError_t e = cudaMemset(w, 0, sizeof(int) * 8);
+    if (e == cudaSuccess)
+        e = cudaLaunchCooperativeKernel((void*)k_barrier_check, n_blocks, NT, args, 0, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(h, w, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(w);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MOT_ERR_CUDA;
+    }
+    *passed = h[7];
+    *timeout_round = h[2];
+    return (h[1] & 4) ? MOT_ERR_TIMEOUT : MOT_OK;
+}

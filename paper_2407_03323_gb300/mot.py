@@ -34,7 +34,7 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
            "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
-           "mot_probe_transpose", "mot_last_error"]
+           "mot_probe_transpose", "mot_barrier_check", "mot_last_error"]
 MOT_PDSA_FP32_SPECTRUM = 1
 MOT_PDSA_FULL_REORTH = 2
 
@@ -98,6 +98,7 @@ def load_library(path=LIB_PATH):
     lib.mot_probe_setup.argtypes = [P, I, P]
     lib.mot_probe_field.argtypes = [P, I, P, P, P]
     lib.mot_probe_transpose.argtypes = [P, I, P, P, P]
+    lib.mot_barrier_check.argtypes = [I, I, I, D, P, P]
     lib.mot_last_error.argtypes = [P]
     lib.mot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -188,6 +189,17 @@ def fma_peak(fp64=True, target_ms=100.0):
             break
         iters = int(min(2 ** 30, iters * target_ms / max(ms.value, 1e-3)))
     return fl.value / (ms.value * 1e-3)
+
+
+def barrier_check(n_blocks, rounds, absent=-1, budget_s=0.2):
+    """One cooperative launch of the solve's grid barrier (mot_barrier_check): returns
+    (status, blocks that passed every round, round of a timeout or 0)."""
+    lib = load_library()
+    passed = ctypes.c_int()
+    rnd = ctypes.c_int()
+    st = lib.mot_barrier_check(n_blocks, rounds, absent, budget_s, ctypes.byref(passed),
+                               ctypes.byref(rnd))
+    return st, passed.value, rnd.value
 
 
 class Context:

@@ -95,3 +95,11 @@ def test_diagnostic_entry_points_reject_bad_arguments_on_the_host(lib):
     assert lib.mot_frequency_response(4, 1, J.ctypes.data, 1.0, 1.5, e_ok.ctypes.data, 0.1,
                                       5.0, 1, f.ctypes.data, out.ctypes.data, None) == 1
     assert lib.mot_fir_magnitude(None, 3, 1, f.ctypes.data, out.ctypes.data) == 1
+
+
+def test_barrier_check_rejects_bad_arguments_on_the_host(lib):
+    """mot_barrier_check validates its counts and budget before any CUDA call."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    for args in ((4, 0, -1, 0.2), (4, 10, 4, 0.2), (4, 10, -2, 0.2), (4, 10, -1, 0.0),
+                 (4, 10, -1, 11.0)):
+        assert lib.mot_barrier_check(*args, ctypes.byref(a), ctypes.byref(b)) == 1, args

@@ -143,3 +143,26 @@ def test_grid_too_large_for_the_device_is_oom(mot):
     with mot.Context(wl.cube(4, 3.0)) as ctx:
         ctx.march(4)
         assert ctx.info()["n_done"] == 4
+
+
+def test_grid_barrier_passes_every_round(mot):
+    """The bounded grid barrier of the solve kernel, every block present: 2000 rounds
+    pass with no timeout."""
+    st, passed, rnd = mot.barrier_check(96, 2000)
+    assert st == mot.MOT_OK and passed == 96 and rnd == 0
+
+
+def test_grid_barrier_wait_runs_out(mot):
+    """A block that never arrives (a barrier that nothing completes): the others' wait
+    runs out after its 0.2 s budget, the launch ends with MOT_ERR_TIMEOUT at round 1,
+    and the device stays usable (a march right after is correct)."""
+    import time
+    t0 = time.perf_counter()
+    st, passed, rnd = mot.barrier_check(96, 50, absent=7, budget_s=0.2)
+    dt = time.perf_counter() - t0
+    assert st == mot.MOT_ERR_TIMEOUT and passed == 0 and rnd == 1
+    assert dt < 10.0
+    ctx = _pulse_ctx(mot)
+    ctx.march(16)
+    assert ctx.info()["n_done"] == 16 and np.isfinite(ctx.info()["last_norm"])
+    ctx.close()
