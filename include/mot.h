@@ -410,7 +410,28 @@ typedef struct {
     double ms_mac;
     double ms_fft_inv;
     double ms_solve;
+    long long graph_launches;        /* periods launched as one CUDA graph (mot_set_graph) */
+    long long graph_instantiations;  /* executable graphs built (first period, or after an
+                                        in-place update was refused)                     */
 } mot_stats;
+
+/*
+ * mot_set_graph - march whole periods as CUDA graphs (no counterpart in the paper:
+ * launch overhead).  With steps_per_graph = Q > 0, mot_march captures the launches of
+ * Q consecutive steps (every step's history transform, far-level firings, near-lag
+ * MAC, inverse transform, epilogue and solve of Eqs. PnFFTMOT and MOTInversion) into a
+ * graph and launches it as one unit.  A period starts at a step n with (n - 1) mod Q = 0
+ * and n >= 2, where every level fires, so the graphs of all periods hold the same
+ * kernels in the same order: the first is instantiated, the later ones update it in
+ * place (ring slots, step index, excitation and output pointers).  Steps outside whole
+ * periods are launched one by one.  Results are identical to mot_march without graphs.
+ * Used only when the excitation is on the device (or fully staged), J_out is NULL or a
+ * device pointer, profiling is off and the stream is not a default stream; otherwise
+ * mot_march launches step by step.  Q = 0 turns graphs off.
+ * Errors: MOT_ERR_ARG (Q < 0 or Q > 65536; with the blocked scheme Q not a multiple of
+ * the longest level's period, see mot_get_info levels).
+ */
+mot_status mot_set_graph(mot_ctx* ctx, int steps_per_graph);
 
 /* Enable (1) or disable (0) per-phase event timing in mot_march and reset the
  * counters.  Timing adds five event records per step. */

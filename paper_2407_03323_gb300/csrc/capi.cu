@@ -73,6 +73,8 @@ void free_all(mot_ctx* c) {
         c->shared_src->n_shared -= 1;
         c->shared_src = nullptr;
     }
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
     for (int a = 0; a < 3; ++a) mot::fft_free_axis(c->ax[a]);
     for (int k = 0; k < 8; ++k) mot::fft_free_axis(c->lev_fft[k]);
     mot::history_free<double>(c);
@@ -493,6 +495,52 @@ mot_status mot_plane_wave(mot_ctx* c, const double k_hat[3], const double p_hat[
     });
 }
 
+}  // extern "C"
+
+namespace {
+
+// Capture the launches of `launch_period` (one period of the march) on s into a graph,
+// update the context's executable graph in place with its arguments (the kernels and
+// their order are the same every period; ring slots, step indices, the excitation and
+// output pointers change), instantiate it on the first period or when the update is
+// refused, and launch it.  Launches already enqueued keep the arguments they had.
+template <typename F>
+void march_period_graph(mot_ctx* c, cudaStream_t s, F&& launch_period) {
+    cudaGraph_t g = nullptr;
+    MOT_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    try {
+        launch_period();
+    } catch (...) {
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        throw;
+    }
+    MOT_CUDA_TRY(cudaStreamEndCapture(s, &g));
+    struct Guard {
+        cudaGraph_t g;
+        ~Guard() { cudaGraphDestroy(g); }
+    } guard{g};
+    if (c->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+    }
+    if (!c->gexec) {
+        MOT_CUDA_TRY(cudaGraphInstantiate(&c->gexec, g, 0));
+        c->stats.graph_instantiations += 1;
+    }
+    MOT_CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+    c->stats.graph_launches += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
 mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
     if (!c) return MOT_ERR_ARG;
     if (c->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
@@ -521,13 +569,19 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
         int waited_chunk = -1;
         MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * mot::kStatusWords, s));
         if (c->profiling) ensure_events(c, 6 * (size_t)n_steps);
-        for (int i = 0; i < n_steps; ++i) {
+        // whole periods as one CUDA graph: device-resident excitation and outputs, no
+        // per-phase events, a capturable stream
+        const bool graphs = c->graph_steps > 0 && !c->profiling && (!J_out || dev_out) &&
+                            s != cudaStreamLegacy && s != cudaStreamPerThread && s != nullptr;
+        if (graphs && c->e_chunk_steps > 0)   // the whole staged excitation, before capture
+            for (cudaEvent_t e : c->e_chunk) MOT_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
+        auto one_step = [&](int i) {
             const int n = c->n_done + 1 + i;
             const double* En = nullptr;
             if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count) {
                 En = c->Estage + (long long)(n - c->E_first) * step;
-                if (c->e_chunk_steps > 0) {   // host excitation still arriving: wait for its chunk
-                    const int j = (n - c->E_first) / c->e_chunk_steps;
+                if (c->e_chunk_steps > 0 && !graphs) {   // host excitation still arriving:
+                    const int j = (n - c->E_first) / c->e_chunk_steps;   // wait for its chunk
                     if (j != waited_chunk) {
                         MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->e_chunk[j], 0));
                         waited_chunk = j;
@@ -560,6 +614,19 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
                     MOT_CUDA_TRY(cudaEventRecord(c->out_done[k], c->cstream));
                 }
                 c->stats.launches += 1;
+            }
+        };
+        for (int i = 0; i < n_steps;) {
+            const int n = c->n_done + 1 + i, Q = c->graph_steps;
+            // a period starts where every level fires ((n - 1) mod Q = 0, Q a multiple
+            // of the longest level), after step 1 (no history transform at n = 1), so all
+            // periods launch the same kernels in the same order with other arguments
+            if (graphs && n >= 2 && (n - 1) % Q == 0 && n_steps - i >= Q) {
+                march_period_graph(c, s, [&] { for (int j = 0; j < Q; ++j) one_step(i + j); });
+                i += Q;
+            } else {
+                one_step(i);
+                ++i;
             }
         }
         std::vector<double> nrm(n_steps);
@@ -909,6 +976,28 @@ mot_status mot_set_solver(mot_ctx* c, double tol, int max_iter, double growth_li
     c->tol = tol;
     c->max_iter = max_iter;
     c->growth = growth_limit;
+    return MOT_OK;
+}
+
+mot_status mot_set_graph(mot_ctx* c, int steps_per_graph) {
+    if (!c) return MOT_ERR_ARG;
+    if (steps_per_graph < 0 || steps_per_graph > 65536) {
+        c->err = "steps_per_graph must be in 0..65536";
+        return MOT_ERR_ARG;
+    }
+    if (steps_per_graph > 0 && c->scheme == MOT_HISTORY_BLOCKED && c->nlev > 0 &&
+        steps_per_graph % c->lev_S[c->nlev - 1] != 0) {
+        char b[160];
+        snprintf(b, sizeof b, "steps_per_graph must be a multiple of the longest level's "
+                 "period %d", c->lev_S[c->nlev - 1]);
+        c->err = b;
+        return MOT_ERR_ARG;
+    }
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+    }
+    c->graph_steps = steps_per_graph;
     return MOT_OK;
 }
 

@@ -178,6 +178,8 @@ struct mot_ctx {
 
     cudaStream_t stream = nullptr;
     int device = 0;              // CUDA device the context was created on
+    int graph_steps = 0;         // steps per CUDA graph of the march (0: no graphs)
+    cudaGraphExec_t gexec = nullptr;   // executable graph of one period, updated in place
 
     // mot_create_shared: setup (geometry, table, spectra, twiddles) borrowed from
     // shared_src, which must outlive this context; n_shared counts the borrowers

@@ -34,7 +34,7 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
            "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
-           "mot_probe_transpose", "mot_barrier_check", "mot_last_error"]
+           "mot_probe_transpose", "mot_barrier_check", "mot_set_graph", "mot_last_error"]
 MOT_PDSA_FP32_SPECTRUM = 1
 MOT_PDSA_FULL_REORTH = 2
 
@@ -44,7 +44,9 @@ class Stats(ctypes.Structure):
                 ("far_launches", ctypes.c_longlong), ("steps", ctypes.c_longlong),
                 ("cg_iters", ctypes.c_longlong), ("ms_fft_fwd", ctypes.c_double),
                 ("ms_far", ctypes.c_double), ("ms_mac", ctypes.c_double),
-                ("ms_fft_inv", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+                ("ms_fft_inv", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("graph_launches", ctypes.c_longlong),
+                ("graph_instantiations", ctypes.c_longlong)]
 
 
 class MotError(RuntimeError):
@@ -99,6 +101,7 @@ def load_library(path=LIB_PATH):
     lib.mot_probe_field.argtypes = [P, I, P, P, P]
     lib.mot_probe_transpose.argtypes = [P, I, P, P, P]
     lib.mot_barrier_check.argtypes = [I, I, I, D, P, P]
+    lib.mot_set_graph.argtypes = [P, I]
     lib.mot_last_error.argtypes = [P]
     lib.mot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -513,6 +516,11 @@ class Context:
         self._check(st)
         return {"ell": ell.value, "P": tuple(P), "n_done": nd.value, "last_norm": ln.value,
                 "fail_step": fs.value, "last_cg_iters": it.value}
+
+    def set_graph(self, steps_per_graph):
+        """March whole periods of steps_per_graph steps as CUDA graphs (mot_set_graph);
+        0 turns graphs off.  For the blocked scheme a multiple of levels[-1]."""
+        self._check(self._lib.mot_set_graph(self._h, int(steps_per_graph)))
 
     def set_profiling(self, enable=True):
         """Per-phase event timing in march and counter reset (mot_set_profiling)."""
