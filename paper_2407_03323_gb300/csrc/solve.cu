@@ -346,15 +346,15 @@ __device__ __forceinline__ void load_halo(const CGArgs& a, const float4* __restr
     }
 }
 
-// One Chebyshev iteration over the tiles of this block: r -= A d_k, e += d_k,
-// d_{k+1} = c1 d_k + c2 r.  The halo of the next tile is copied into the other shared
+// One Chebyshev iteration over the tiles of this block: r -= A d_k, e += d_k (e = d_0
+// on the first iteration, so e needs no clearing), d_{k+1} = c1 d_k + c2 r.  The halo of the next tile is copied into the other shared
 // buffer while the current one is computed, and each thread loads its voxels' own
 // e, r and diagonal before waiting for the halo.
 constexpr int kVoxPerThread = TT * TT * TT / NT;
 static_assert(kVoxPerThread * NT == TT * TT * TT, "tile voxels per thread");
 __device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* __restrict__ dk,
                                                 float4* __restrict__ dn, float c1, float c2,
-                                                float4 (*sd)[TH * TH * TH]) {
+                                                bool first, float4 (*sd)[TH * TH * TH]) {
     const long long UV = (long long)a.U * a.V;
     int tile = blockIdx.x;
     if (tile < a.ntiles) load_halo(a, dk, sd[0], a.tiles[tile]);
@@ -380,7 +380,7 @@ __device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* _
                 dgv[v] = a.diag32[m];
                 if (dgv[v] != 0.f) {
                     mv[v] = m;
-                    ev[v] = a.e[m];
+                    ev[v] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : a.e[m];
                     rv[v] = a.r[m];
                 }
             }
@@ -422,8 +422,8 @@ __device__ __forceinline__ void cheb_pass_tiled(const CGArgs& a, const float4* _
 // Double-float residual pass on the 8^3 tiles (FP32-history): the two halves of the
 // shared halo buffer hold the hi and lo parts of x around the tile (zero outside the
 // grid and on inactive voxels, so no neighbour mask is needed).  Writes r (rounded to
-// FP32) on active voxels and adds |r|^2 (and, on the first pass, |b|^2 in FP64) to the
-// thread's partial sums.
+// FP32) and the first Chebyshev direction d_0 = r / theta on active voxels and adds
+// |r|^2 (and, on the first pass, |b|^2 in FP64) to the thread's partial sums.
 __device__ __forceinline__ void residual_df_tiled(const CGArgs& a, float4 (*sd)[TH * TH * TH],
                                                   double& rr_p, double& bb_p, bool first) {
     const long long UV = (long long)a.U * a.V;
@@ -476,6 +476,7 @@ __device__ __forceinline__ void residual_df_tiled(const CGArgs& a, float4 (*sd)[
                                                   blv[v], load, 0);
             rr_p += (double)r.x * r.x + (double)r.y * r.y + (double)r.z * r.z;
             a.r[mv[v]] = r;
+            a.p[mv[v]] = make_float4(r.x * a.inv_theta, r.y * a.inv_theta, r.z * a.inv_theta, 0.f);
         }
         __syncthreads();
     }
@@ -508,8 +509,16 @@ __device__ __forceinline__ void block_sum2(double& a, double& b) {
 __device__ __forceinline__ double grid_total(const double* red, int nb) {
     __shared__ double s_tot;
     if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int k = threadIdx.x; k < nb; k += 32) v += __ldcg(red + k);
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;   // four independent loads in flight
+        int k = threadIdx.x;
+        for (; k + 96 < nb; k += 128) {
+            v0 += __ldcg(red + k);
+            v1 += __ldcg(red + k + 32);
+            v2 += __ldcg(red + k + 64);
+            v3 += __ldcg(red + k + 96);
+        }
+        for (; k < nb; k += 32) v0 += __ldcg(red + k);
+        double v = (v0 + v1) + (v2 + v3);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (threadIdx.x == 0) s_tot = v;
     }
@@ -568,6 +577,22 @@ __device__ bool grid_barrier(unsigned* bar, long long budget, int* status, int s
     return s_ok != 0;
 }
 
+// for i = t0, t0 + gs, ... < n: U indices per round, ld(i) for all of them before
+// st(i, value) for any (the loads of a round are independent requests in flight)
+template <int U, typename Ld, typename St>
+__device__ __forceinline__ void grid_loop(long long t0, long long n, long long gs, Ld&& ld,
+                                          St&& st) {
+    for (long long i0 = t0; i0 < n; i0 += U * gs) {
+        decltype(ld(0LL)) v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * gs < n) v[u] = ld(i0 + u * gs);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * gs < n) st(i0 + u * gs, v[u]);
+    }
+}
+
 // Check of the barrier's bounded wait: every block passes `rounds` barriers, except the
 // block `absent` (>= 0), which returns at once; the others' wait then runs out.
 // w[1] flags, w[2] the round of a timeout, w[4..6] the barrier, w[7] blocks that
@@ -599,26 +624,43 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
     double bb = 0.0, rr = 0.0;
     int its = 0, outer = 0;
     bool first = true, converged = false, zeroed = false, nonfinite = false;
+    // grid-stride loops over the active voxels (or all voxels) take four indices per
+    // thread per round and issue all their loads before the first store, so that a
+    // thread has several independent memory requests in flight
+    struct XB { int m; double x0, x1, x2, b0, b1, b2; };
+    struct RF { int m; float4 r; };
+    struct RD { int m; double r0, r1, r2; };
+    struct EHL { int m; float4 e, h, l; };
+    struct EX3 { int m; float4 e; double x0, x1, x2; };
+    struct HL { int m; float4 h, l; };
+    struct X3 { double x0, x1, x2; };
     if (DF) {
-        for (long long i = t0; i < a.nact; i += gs) {
-            const int m = a.act[i];
-            float4 h, l;
-            df_split(a.x[m], h.x, l.x);
-            df_split(a.x[M + m], h.y, l.y);
-            df_split(a.x[2 * M + m], h.z, l.z);
-            h.w = l.w = 0.f;
-            a.xh[m] = h;
-            a.xl[m] = l;
-            df_split(a.b[m], h.x, l.x);
-            df_split(a.b[M + m], h.y, l.y);
-            df_split(a.b[2 * M + m], h.z, l.z);
-            a.bh[m] = h;
-            a.bl[m] = l;
-        }
+        grid_loop<1>(t0, a.nact, gs,
+            [&](long long i) {
+                XB v;
+                v.m = a.act[i];
+                v.x0 = a.x[v.m]; v.x1 = a.x[M + v.m]; v.x2 = a.x[2 * M + v.m];
+                v.b0 = a.b[v.m]; v.b1 = a.b[M + v.m]; v.b2 = a.b[2 * M + v.m];
+                return v;
+            },
+            [&](long long, const XB& v) {
+                float4 h, l;
+                df_split(v.x0, h.x, l.x);
+                df_split(v.x1, h.y, l.y);
+                df_split(v.x2, h.z, l.z);
+                h.w = l.w = 0.f;
+                a.xh[v.m] = h;
+                a.xl[v.m] = l;
+                df_split(v.b0, h.x, l.x);
+                df_split(v.b1, h.y, l.y);
+                df_split(v.b2, h.z, l.z);
+                a.bh[v.m] = h;
+                a.bl[v.m] = l;
+            });
         if (!gsync()) return;
     }
     while (true) {
-        // ---- residual (FP64, or double-float rounded to FP32)
+        // ---- residual (FP64, or double-float rounded to FP32 with d_0 = r / theta)
         double rr_p = 0.0, bb_p = 0.0;
         if (DF) residual_df_tiled(a, sd, rr_p, bb_p, first);
         for (long long i = t0; !DF && i < a.nact; i += gs) {
@@ -643,7 +685,9 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         rr = grid_total(red0, nb);
         if (first) bb = grid_total(red1, nb);
         first = false;
-        if (!gsync()) return;   // all blocks have read red0/red1
+        // red0 / red1 are written next after at least one more barrier (the next
+        // residual follows the Chebyshev passes; the final norm follows the merge or
+        // its own barrier), so no barrier is needed here for their readers
         if (!(rr <= 1e300) || !(bb <= 1e300)) {
             // NaN or Inf in the right-hand side (or the start): no iteration can help;
             // J_n is returned as NaN so that the monitor and the caller see it
@@ -666,83 +710,118 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         }
         if (rr <= a.tol2 * bb) { converged = true; break; }
         if (outer >= a.max_outer || its >= a.max_iter) break;
-        // ---- FP32 Chebyshev iteration for A e = r / ||r|| (r holds the FP32 residual).
+        // ---- FP32 Chebyshev iteration for A e = r (r holds the FP32 residual).
         // One fused pass per iteration (apply to d_k, update e, r, d_{k+1}) and one grid
         // barrier; d is double-buffered because neighbours read d_k during the pass.
         // iterations for the reduction still needed (with a factor 10 of margin), never
         // asking for more than FP32 can deliver in one refinement (5e-6)
         const double need = fmax(0.1 * sqrt(a.tol2 * bb / rr), 5e-6);
         const int n_it = min(a.n_cheb, max(3, (int)ceil(log(0.5 * need) / a.log_rate)));
-        // normalise in FP64 first: a tiny residual must not underflow in FP32
-        const double sc = 1.0 / sqrt(rr);
-        const float sc32 = (float)sc;
-        for (long long i = t0; i < a.nact; i += gs) {
-            const int m = a.act[i];
-            float4 rv;
-            if (DF) {
-                rv = a.r[m];
-                rv.x *= sc32; rv.y *= sc32; rv.z *= sc32;
+        // The double-float residual is already an FP32 vector with d_0 beside it; it is
+        // iterated as it is unless its norm is far from 1 (FP32 range).  Otherwise (and
+        // always for the FP64 residual) r is first scaled to unit norm in FP64, so that
+        // a tiny residual cannot underflow in FP32, and e is scaled back by ||r||.
+        const bool scaled = !DF || !(rr >= 1e-40 && rr <= 1e40);
+        const double sc = scaled ? 1.0 / sqrt(rr) : 1.0;
+        if (scaled) {
+            const float sc32 = (float)sc;
+            if constexpr (DF) {
+                grid_loop<4>(t0, a.nact, gs,
+                    [&](long long i) { const int m = a.act[i]; return RF{m, a.r[m]}; },
+                    [&](long long, const RF& v) {
+                        const float4 rv = make_float4(v.r.x * sc32, v.r.y * sc32, v.r.z * sc32, 0.f);
+                        a.r[v.m] = rv;
+                        a.p[v.m] = make_float4(rv.x * a.inv_theta, rv.y * a.inv_theta,
+                                               rv.z * a.inv_theta, 0.f);
+                    });
             } else {
-                rv = make_float4((float)(a.r64[m] * sc), (float)(a.r64[M + m] * sc),
-                                 (float)(a.r64[2 * M + m] * sc), 0.f);
+                grid_loop<4>(t0, a.nact, gs,
+                    [&](long long i) {
+                        const int m = a.act[i];
+                        return RD{m, a.r64[m], a.r64[M + m], a.r64[2 * M + m]};
+                    },
+                    [&](long long, const RD& v) {
+                        const float4 rv = make_float4((float)(v.r0 * sc), (float)(v.r1 * sc),
+                                                      (float)(v.r2 * sc), 0.f);
+                        a.r[v.m] = rv;
+                        a.p[v.m] = make_float4(rv.x * a.inv_theta, rv.y * a.inv_theta,
+                                               rv.z * a.inv_theta, 0.f);
+                    });
             }
-            a.r[m] = rv;
-            a.p[m] = make_float4(rv.x * a.inv_theta, rv.y * a.inv_theta, rv.z * a.inv_theta, 0.f);
-            a.e[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!gsync()) return;
         }
-        if (!gsync()) return;
         float4* dk = a.p;
         float4* dn = a.q;
         for (int k = 0; k < n_it; ++k) {
-            cheb_pass_tiled(a, dk, dn, a.c1[k], a.c2[k], sd);
+            cheb_pass_tiled(a, dk, dn, a.c1[k], a.c2[k], k == 0, sd);
             if (!gsync()) return;
             float4* t = dk; dk = dn; dn = t;
         }
         its += n_it;
-        // ---- correction x += ||r|| e (FP64, or in float pairs)
-        const double back = sqrt(rr);
+        // ---- correction x += (1 / sc) e (FP64, or in float pairs)
+        const double back = 1.0 / sc;
         float bkh, bkl;
         df_split(back, bkh, bkl);
-        for (long long i = t0; i < a.nact; i += gs) {
-            const int m = a.act[i];
-            const float4 ev = a.e[m];
-            if (DF) {
-                float4 h = a.xh[m], l = a.xl[m];
-                const float ec[3] = {ev.x, ev.y, ev.z};
-                float hc[3] = {h.x, h.y, h.z}, lc[3] = {l.x, l.y, l.z};
+        if constexpr (DF) {
+            grid_loop<1>(t0, a.nact, gs,
+                [&](long long i) {
+                    const int m = a.act[i];
+                    return EHL{m, a.e[m], a.xh[m], a.xl[m]};
+                },
+                [&](long long, const EHL& v) {
+                    const float ec[3] = {v.e.x, v.e.y, v.e.z};
+                    float hc[3] = {v.h.x, v.h.y, v.h.z}, lc[3] = {v.l.x, v.l.y, v.l.z};
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float p = __fmul_rn(bkh, ec[c]);
-                    const float pe = __fmaf_rn(bkh, ec[c], -p) + __fmul_rn(bkl, ec[c]);
-                    df_add(hc[c], lc[c], p, pe);
-                }
-                a.xh[m] = make_float4(hc[0], hc[1], hc[2], 0.f);
-                a.xl[m] = make_float4(lc[0], lc[1], lc[2], 0.f);
-            } else {
-                a.x[m] += back * (double)ev.x;
-                a.x[M + m] += back * (double)ev.y;
-                a.x[2 * M + m] += back * (double)ev.z;
-            }
+                    for (int c = 0; c < 3; ++c) {
+                        const float p = __fmul_rn(bkh, ec[c]);
+                        const float pe = __fmaf_rn(bkh, ec[c], -p) + __fmul_rn(bkl, ec[c]);
+                        df_add(hc[c], lc[c], p, pe);
+                    }
+                    a.xh[v.m] = make_float4(hc[0], hc[1], hc[2], 0.f);
+                    a.xl[v.m] = make_float4(lc[0], lc[1], lc[2], 0.f);
+                });
+        } else {
+            grid_loop<4>(t0, a.nact, gs,
+                [&](long long i) {
+                    const int m = a.act[i];
+                    return EX3{m, a.e[m], a.x[m], a.x[M + m], a.x[2 * M + m]};
+                },
+                [&](long long, const EX3& v) {
+                    a.x[v.m] = v.x0 + back * (double)v.e.x;
+                    a.x[M + v.m] = v.x1 + back * (double)v.e.y;
+                    a.x[2 * M + v.m] = v.x2 + back * (double)v.e.z;
+                });
         }
         if (!gsync()) return;
         ++outer;
     }
     if (DF && !zeroed && !nonfinite) {   // x = hi + lo back in FP64
-        for (long long i = t0; i < a.nact; i += gs) {
-            const int m = a.act[i];
-            const float4 h = a.xh[m], l = a.xl[m];
-            a.x[m] = (double)h.x + (double)l.x;
-            a.x[M + m] = (double)h.y + (double)l.y;
-            a.x[2 * M + m] = (double)h.z + (double)l.z;
-        }
+        grid_loop<4>(t0, a.nact, gs,
+            [&](long long i) {
+                HL v;
+                v.m = a.act[i];
+                v.h = a.xh[v.m];
+                v.l = a.xl[v.m];
+                return v;
+            },
+            [&](long long, const HL& v) {
+                a.x[v.m] = (double)v.h.x + (double)v.l.x;
+                a.x[M + v.m] = (double)v.h.y + (double)v.l.y;
+                a.x[2 * M + v.m] = (double)v.h.z + (double)v.l.z;
+            });
         if (!gsync()) return;
     }
     // x written above is read by other blocks below
     if ((zeroed || nonfinite) && !gsync()) return;
     // norm of the solution (all voxels, active and not)
     double xx = 0.0, dummy = 0.0;
-    for (long long m = t0; m < M; m += gs)
-        for (int c = 0; c < 3; ++c) xx += a.x[c * M + m] * a.x[c * M + m];
+    grid_loop<4>(t0, M, gs,
+        [&](long long m) {
+            X3 v;
+            v.x0 = a.x[m]; v.x1 = a.x[M + m]; v.x2 = a.x[2 * M + m];
+            return v;
+        },
+        [&](long long, const X3& v) { xx += v.x0 * v.x0 + v.x1 * v.x1 + v.x2 * v.x2; });
     block_sum2(xx, dummy);
     if (!gsync()) return;
     if (threadIdx.x == 0) red0[blockIdx.x] = xx;
