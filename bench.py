@@ -21,7 +21,8 @@ Besides the contract's keys, each variant reports its phase times (CUDA events o
 march stream), the roofline of its dominant history kernel, and a timing-only
 comparison of its forward FFT phase with cuFFT (torch.fft.rfftn) on the full padded
 grid.  `e2e` marches one bench step from pinned host excitation to pinned host J
-through the library's overlapped transfers.
+through the library's overlapped transfers (timed after one untimed call through the
+same buffers).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -383,6 +384,10 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
         Eh.copy_(E[:k].cpu())
         Jh = torch.empty((k, M, 3), dtype=torch.float64).pin_memory()
         del E
+        # one untimed call through the same host buffers first (first touch of the
+        # pinned pages by the copy engines), then the timed one
+        ctx.set_excitation(Eh, stream=stream)
+        ctx.march(k, out=Jh, stream=stream)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()

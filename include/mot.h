@@ -416,6 +416,32 @@ typedef struct {
 } mot_stats;
 
 /*
+ * Several right-hand sides of one scatterer (the n_rhs dimension of the excitation):
+ * the excitations E^(r) of Eq. E for r < n_rhs, marched by Eq. MOTInversion with the
+ * same Z_l, each its own march state.
+ * mot_set_excitation_rhs - stage E for the context's n_rhs right-hand sides.  E is
+ *   [r][n_steps][M][3] (host or device, read during the call or on the stream as for
+ *   mot_set_excitation): right-hand side 0 is the context itself, the others are
+ *   contexts sharing its setup (made here, owned and destroyed with it).  n_rhs may
+ *   change only before the first step.  Errors: MOT_ERR_ARG (n_rhs outside 1..4096,
+ *   n_steps < 1, NULL E, ctx made by mot_create_shared, n_rhs changed after marching),
+ *   MOT_ERR_OOM, MOT_ERR_CUDA.
+ * mot_march_rhs - march every right-hand side n_steps steps, the steps of all of them
+ *   interleaved on their own streams (all on `stream` when it is not NULL); J_out is
+ *   [r][n_steps][M][3] (host or device) or NULL.  Returns the first failing right-hand
+ *   side's status (mot_last_error names it); each one's monitor state is its own
+ *   (mot_rhs_context + mot_get_info).  Graph-captured periods are not used here.
+ * mot_rhs_context - the context of right-hand side k (k = 0: ctx itself), owned by ctx,
+ *   for per-right-hand-side queries (mot_get_info, mot_get_stats, mot_restart ...).
+ *   Errors: MOT_ERR_ARG (k outside 0..n_rhs - 1).
+ * mot_set_solver on ctx applies to all its right-hand sides.
+ */
+mot_status mot_set_excitation_rhs(mot_ctx* ctx, int n_rhs, int n_steps, const double* E,
+                                  void* stream);
+mot_status mot_march_rhs(mot_ctx* ctx, int n_steps, double* J_out, void* stream);
+mot_status mot_rhs_context(mot_ctx* ctx, int k, mot_ctx** out);
+
+/*
  * mot_set_graph - march whole periods as CUDA graphs (no counterpart in the paper:
  * launch overhead).  With steps_per_graph = Q > 0, mot_march captures the launches of
  * Q consecutive steps (every step's history transform, far-level firings, near-lag

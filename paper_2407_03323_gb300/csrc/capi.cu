@@ -342,6 +342,11 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
 void mot_destroy(mot_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();
+    for (mot_ctx* r : c->rhs_ctx) {   // they borrow this context's setup
+        free_all(r);
+        delete r;
+    }
+    c->rhs_ctx.clear();
     free_all(c);
     delete c;
 }
@@ -537,18 +542,23 @@ void march_period_graph(mot_ctx* c, cudaStream_t s, F&& launch_period) {
     c->stats.graph_launches += 1;
 }
 
-}  // namespace
-
-extern "C" {
-
-mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
-    if (!c) return MOT_ERR_ARG;
-    if (c->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
-    if (n_steps < 1) { c->err = "n_steps must be >= 1"; return MOT_ERR_ARG; }
+// One mot_march call on one context, in stages so that several contexts (the
+// right-hand sides of mot_march_rhs) can interleave their launches: begin() sizes the
+// buffers and clears the device status; launch_step(i) / launch_all() enqueue the
+// steps on the context's stream; fetch() waits for the stream, reads the per-step
+// norms and the solve's status words and applies the stability monitor (Sec. 5.2).
+struct MarchRun {
+    mot_ctx* c;
+    int n_steps;
+    double* J_out;
+    cudaStream_t s;
+    bool dev_out = false, graphs = false, graphs_allowed = true;
+    int waited_chunk = -1;
+    long long step = 0;
     mot_status result = MOT_OK;
-    mot_status st = guarded(c, [&] {
-        cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-        const bool dev_out = is_device_ptr(J_out);
+
+    void begin() {
+        dev_out = is_device_ptr(J_out);
         if (n_steps > c->norms_cap) {
             MOT_CUDA_TRY(cudaStreamSynchronize(s));
             cudaFree(c->norms);
@@ -557,7 +567,7 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
             MOT_CUDA_TRY(cudaMalloc(&c->norms, sizeof(double) * n_steps));
             c->norms_cap = n_steps;
         }
-        const long long step = 3 * c->M;
+        step = 3 * c->M;
         if (J_out && !dev_out) {
             if (!c->outbuf) MOT_CUDA_TRY(cudaMalloc(&c->outbuf, sizeof(double) * step * kOutSlots));
             ensure_copy_stream(c);
@@ -566,69 +576,75 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
                 if (!c->out_done[k]) c->out_done[k] = new_sync_event();
             }
         }
-        int waited_chunk = -1;
         MOT_CUDA_TRY(cudaMemsetAsync(c->dstatus, 0, sizeof(int) * mot::kStatusWords, s));
         if (c->profiling) ensure_events(c, 6 * (size_t)n_steps);
         // whole periods as one CUDA graph: device-resident excitation and outputs, no
         // per-phase events, a capturable stream
-        const bool graphs = c->graph_steps > 0 && !c->profiling && (!J_out || dev_out) &&
-                            s != cudaStreamLegacy && s != cudaStreamPerThread && s != nullptr;
+        graphs = graphs_allowed && c->graph_steps > 0 && !c->profiling && (!J_out || dev_out) &&
+                 s != cudaStreamLegacy && s != cudaStreamPerThread && s != nullptr;
         if (graphs && c->e_chunk_steps > 0)   // the whole staged excitation, before capture
             for (cudaEvent_t e : c->e_chunk) MOT_CUDA_TRY(cudaStreamWaitEvent(s, e, 0));
-        auto one_step = [&](int i) {
-            const int n = c->n_done + 1 + i;
-            const double* En = nullptr;
-            if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count) {
-                En = c->Estage + (long long)(n - c->E_first) * step;
-                if (c->e_chunk_steps > 0 && !graphs) {   // host excitation still arriving:
-                    const int j = (n - c->E_first) / c->e_chunk_steps;   // wait for its chunk
-                    if (j != waited_chunk) {
-                        MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->e_chunk[j], 0));
-                        waited_chunk = j;
-                    }
+    }
+
+    void launch_step(int i) {
+        const int n = c->n_done + 1 + i;
+        const double* En = nullptr;
+        if (c->E_count > 0 && n >= c->E_first && n < c->E_first + c->E_count) {
+            En = c->Estage + (long long)(n - c->E_first) * step;
+            if (c->e_chunk_steps > 0 && !graphs) {   // host excitation still arriving:
+                const int j = (n - c->E_first) / c->e_chunk_steps;   // wait for its chunk
+                if (j != waited_chunk) {
+                    MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->e_chunk[j], 0));
+                    waited_chunk = j;
                 }
             }
-            cudaEvent_t* ev = c->profiling ? &c->events[6 * (size_t)i] : nullptr;
-            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
-            history_for(c, n, s, ev ? ev + 1 : nullptr);
-            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[4], s));
-            mot::solve_step(c, n, En, c->norms + i, s);
-            c->stats.launches += 2;
-            if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[5], s));
-            if (J_out) {
-                double* dst = J_out + (long long)i * 3 * c->M;
-                if (dev_out) {
-                    mot::write_aos(c, n, dst, s);
-                } else {
-                    // AoS copy into ring slot k on s, device-to-host copy on the copy
-                    // stream, overlapped with the next steps; slot k is rewritten only
-                    // after its previous copy has finished
-                    const int k = i % kOutSlots;
-                    double* slot = c->outbuf + (long long)k * step;
-                    MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->out_done[k], 0));
-                    mot::write_aos(c, n, slot, s);
-                    MOT_CUDA_TRY(cudaEventRecord(c->out_ready[k], s));
-                    MOT_CUDA_TRY(cudaStreamWaitEvent(c->cstream, c->out_ready[k], 0));
-                    MOT_CUDA_TRY(cudaMemcpyAsync(dst, slot, sizeof(double) * step,
-                                                 cudaMemcpyDeviceToHost, c->cstream));
-                    MOT_CUDA_TRY(cudaEventRecord(c->out_done[k], c->cstream));
-                }
-                c->stats.launches += 1;
+        }
+        cudaEvent_t* ev = c->profiling ? &c->events[6 * (size_t)i] : nullptr;
+        if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[0], s));
+        history_for(c, n, s, ev ? ev + 1 : nullptr);
+        if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[4], s));
+        mot::solve_step(c, n, En, c->norms + i, s);
+        c->stats.launches += 2;
+        if (ev) MOT_CUDA_TRY(cudaEventRecord(ev[5], s));
+        if (J_out) {
+            double* dst = J_out + (long long)i * 3 * c->M;
+            if (dev_out) {
+                mot::write_aos(c, n, dst, s);
+            } else {
+                // AoS copy into ring slot k on s, device-to-host copy on the copy
+                // stream, overlapped with the next steps; slot k is rewritten only
+                // after its previous copy has finished
+                const int k = i % kOutSlots;
+                double* slot = c->outbuf + (long long)k * step;
+                MOT_CUDA_TRY(cudaStreamWaitEvent(s, c->out_done[k], 0));
+                mot::write_aos(c, n, slot, s);
+                MOT_CUDA_TRY(cudaEventRecord(c->out_ready[k], s));
+                MOT_CUDA_TRY(cudaStreamWaitEvent(c->cstream, c->out_ready[k], 0));
+                MOT_CUDA_TRY(cudaMemcpyAsync(dst, slot, sizeof(double) * step,
+                                             cudaMemcpyDeviceToHost, c->cstream));
+                MOT_CUDA_TRY(cudaEventRecord(c->out_done[k], c->cstream));
             }
-        };
+            c->stats.launches += 1;
+        }
+    }
+
+    void launch_all() {
         for (int i = 0; i < n_steps;) {
             const int n = c->n_done + 1 + i, Q = c->graph_steps;
             // a period starts where every level fires ((n - 1) mod Q = 0, Q a multiple
             // of the longest level), after step 1 (no history transform at n = 1), so all
             // periods launch the same kernels in the same order with other arguments
             if (graphs && n >= 2 && (n - 1) % Q == 0 && n_steps - i >= Q) {
-                march_period_graph(c, s, [&] { for (int j = 0; j < Q; ++j) one_step(i + j); });
+                march_period_graph(c, s, [&] { for (int j = 0; j < Q; ++j) launch_step(i + j); });
                 i += Q;
             } else {
-                one_step(i);
+                launch_step(i);
                 ++i;
             }
         }
+    }
+
+    void fetch() {
         std::vector<double> nrm(n_steps);
         int hs[4];
         MOT_CUDA_TRY(cudaMemcpyAsync(nrm.data(), c->norms, sizeof(double) * n_steps,
@@ -692,8 +708,24 @@ mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
                      c->max_iter, hs[2]);
             c->err = b;
         }
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+mot_status mot_march(mot_ctx* c, int n_steps, double* J_out, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (c->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
+    if (n_steps < 1) { c->err = "n_steps must be >= 1"; return MOT_ERR_ARG; }
+    MarchRun run{c, n_steps, J_out, stream ? (cudaStream_t)stream : c->stream};
+    mot_status st = guarded(c, [&] {
+        run.begin();
+        run.launch_all();
+        run.fetch();
     });
-    return st != MOT_OK ? st : result;
+    return st != MOT_OK ? st : run.result;
 }
 
 mot_status mot_eval_history(mot_ctx* c, int n_hist, const double* J_hist, double* P_out,
@@ -976,6 +1008,127 @@ mot_status mot_set_solver(mot_ctx* c, double tol, int max_iter, double growth_li
     c->tol = tol;
     c->max_iter = max_iter;
     c->growth = growth_limit;
+    for (mot_ctx* r : c->rhs_ctx) {   // the context's other right-hand sides alike
+        r->tol = tol;
+        r->max_iter = max_iter;
+        r->growth = growth_limit;
+    }
+    return MOT_OK;
+}
+
+mot_status mot_set_excitation_rhs(mot_ctx* c, int n_rhs, int n_steps, const double* E,
+                                  void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_rhs < 1 || n_rhs > 4096 || n_steps < 1 || !E) {
+        c->err = "n_rhs in 1..4096, n_steps >= 1 and E non-null required";
+        return MOT_ERR_ARG;
+    }
+    if (c->shared_src) {
+        c->err = "right-hand sides belong to the context that owns the setup";
+        return MOT_ERR_ARG;
+    }
+    const int have = 1 + (int)c->rhs_ctx.size();
+    if (n_rhs != have) {
+        bool fresh = c->n_done == 0;
+        for (mot_ctx* r : c->rhs_ctx) fresh = fresh && r->n_done == 0;
+        if (!fresh) {
+            char b[160];
+            snprintf(b, sizeof b, "the number of right-hand sides (%d) can change only before "
+                     "the first step", have);
+            c->err = b;
+            return MOT_ERR_ARG;
+        }
+        while ((int)c->rhs_ctx.size() > n_rhs - 1) {
+            mot_ctx* r = c->rhs_ctx.back();
+            cudaDeviceSynchronize();
+            free_all(r);
+            delete r;
+            c->rhs_ctx.pop_back();
+        }
+        while ((int)c->rhs_ctx.size() < n_rhs - 1) {
+            mot_ctx* r = nullptr;
+            const mot_status st = mot_create_shared(c, &r);
+            if (st != MOT_OK) {
+                c->err = g_create_error;
+                return st;
+            }
+            r->max_iter = c->max_iter; r->tol = c->tol; r->growth = c->growth;
+            r->graph_steps = c->graph_steps;
+            c->rhs_ctx.push_back(r);
+        }
+    }
+    // every right-hand side is staged on one stream (the caller's, else this
+    // context's, on which a device E was typically written), and each right-hand
+    // side's own stream then waits for that staging
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const long long per = 3LL * c->M * n_steps;
+    for (int k = 0; k < n_rhs; ++k) {
+        mot_ctx* r = k == 0 ? c : c->rhs_ctx[k - 1];
+        const mot_status st = mot_set_excitation(r, n_steps, E + k * per, s);
+        if (st != MOT_OK) {
+            if (r != c) c->err = r->err;
+            return st;
+        }
+    }
+    return guarded(c, [&] {
+        cudaEvent_t staged = new_sync_event();
+        MOT_CUDA_TRY(cudaEventRecord(staged, s));
+        for (int k = 0; k < n_rhs; ++k) {
+            mot_ctx* r = k == 0 ? c : c->rhs_ctx[k - 1];
+            if (r->stream != s) MOT_CUDA_TRY(cudaStreamWaitEvent(r->stream, staged, 0));
+        }
+        cudaEventDestroy(staged);
+    });
+}
+
+mot_status mot_march_rhs(mot_ctx* c, int n_steps, double* J_out, void* stream) {
+    if (!c) return MOT_ERR_ARG;
+    if (n_steps < 1) { c->err = "n_steps must be >= 1"; return MOT_ERR_ARG; }
+    std::vector<mot_ctx*> all{c};
+    for (mot_ctx* r : c->rhs_ctx) all.push_back(r);
+    for (mot_ctx* r : all) {
+        if (r->broken) return MOT_ERR_STATE;
+        if (r->adj_total) { c->err = "an adjoint run is open (mot_adjoint_end first)"; return MOT_ERR_ARG; }
+        if (r->n_done != c->n_done) { c->err = "right-hand sides out of step"; return MOT_ERR_ARG; }
+    }
+    const long long per = 3LL * c->M * n_steps;
+    std::vector<MarchRun> runs;
+    for (size_t k = 0; k < all.size(); ++k)
+        runs.push_back(MarchRun{all[k], n_steps, J_out ? J_out + (long long)k * per : nullptr,
+                                stream ? (cudaStream_t)stream : all[k]->stream});
+    // the steps of all right-hand sides interleaved, each on its own stream
+    mot_status st = guarded(c, [&] {
+        for (MarchRun& r : runs) {
+            r.graphs_allowed = false;
+            r.begin();
+        }
+        for (int i = 0; i < n_steps; ++i)
+            for (MarchRun& r : runs) r.launch_step(i);
+    });
+    mot_status result = st;
+    for (size_t k = 0; k < runs.size(); ++k) {
+        const mot_status sk = guarded(all[k], [&] { runs[k].fetch(); });
+        const mot_status rk = sk != MOT_OK ? sk : runs[k].result;
+        if (result == MOT_OK && rk != MOT_OK) {
+            result = rk;
+            if (k) {
+                char b[64];
+                snprintf(b, sizeof b, "right-hand side %d: ", (int)k);
+                c->err = b + all[k]->err;
+            }
+        }
+    }
+    return result;
+}
+
+mot_status mot_rhs_context(mot_ctx* c, int k, mot_ctx** out) {
+    if (!c || !out) return MOT_ERR_ARG;
+    *out = nullptr;
+    if (k < 0 || k > (int)c->rhs_ctx.size()) {
+        c->err = "right-hand side index out of range";
+        return MOT_ERR_ARG;
+    }
+    *out = k == 0 ? c : c->rhs_ctx[k - 1];
     return MOT_OK;
 }
 

@@ -34,7 +34,8 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
            "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
-           "mot_probe_transpose", "mot_barrier_check", "mot_set_graph", "mot_last_error"]
+           "mot_probe_transpose", "mot_barrier_check", "mot_set_graph",
+           "mot_set_excitation_rhs", "mot_march_rhs", "mot_rhs_context", "mot_last_error"]
 MOT_PDSA_FP32_SPECTRUM = 1
 MOT_PDSA_FULL_REORTH = 2
 
@@ -102,6 +103,9 @@ def load_library(path=LIB_PATH):
     lib.mot_probe_transpose.argtypes = [P, I, P, P, P]
     lib.mot_barrier_check.argtypes = [I, I, I, D, P, P]
     lib.mot_set_graph.argtypes = [P, I]
+    lib.mot_set_excitation_rhs.argtypes = [P, I, I, P, P]
+    lib.mot_march_rhs.argtypes = [P, I, P, P]
+    lib.mot_rhs_context.argtypes = [P, I, P]
     lib.mot_last_error.argtypes = [P]
     lib.mot_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -259,7 +263,10 @@ class Context:
 
     def close(self):
         """Destroy the context (mot_destroy); refused while contexts shared from it
-        are alive."""
+        are alive.  A right-hand-side view (rhs) only drops its handle."""
+        if getattr(self, "_borrowed", False):
+            self._h = None
+            return
         if getattr(self, "_h", None):
             live = [r() for r in getattr(self, "_shares", [])]
             if any(c is not None and getattr(c, "_h", None) for c in live):
@@ -287,6 +294,42 @@ class Context:
             raise TypeError("E must be float64")
         n = E.shape[0]
         self._check(self._lib.mot_set_excitation(self._h, n, _ptr(E), _stream(stream)))
+
+    def set_excitation_rhs(self, E, stream=None):
+        """Stage E[r][n][M][3] (float64) for E.shape[0] right-hand sides
+        (mot_set_excitation_rhs); right-hand side 0 is this context."""
+        if not _dtype_ok(E):
+            raise TypeError("E must be float64")
+        n_rhs, n = E.shape[0], E.shape[1]
+        self._check(self._lib.mot_set_excitation_rhs(self._h, n_rhs, n, _ptr(E), _stream(stream)))
+        self._n_rhs = n_rhs
+
+    def march_rhs(self, n_steps, out="host", stream=None):
+        """March every right-hand side n_steps steps, interleaved (mot_march_rhs); out
+        'host' returns J[r][n][M][3], None keeps J on the device, or pass a buffer."""
+        n_rhs = getattr(self, "_n_rhs", 1)
+        if isinstance(out, str):
+            out = np.zeros((n_rhs, n_steps, self.M, 3))
+        if out is not None and not _dtype_ok(out):
+            raise TypeError("out must be float64")
+        self._check(self._lib.mot_march_rhs(self._h, n_steps, _ptr(out), _stream(stream)))
+        return out
+
+    def rhs(self, k):
+        """The context of right-hand side k (mot_rhs_context), owned by this one: valid
+        while this context is open."""
+        out = ctypes.c_void_p()
+        self._check(self._lib.mot_rhs_context(self._h, int(k), ctypes.byref(out)))
+        if k == 0:
+            return self
+        c = Context.__new__(Context)
+        c.shape, c.M, c._lib = self.shape, self.M, self._lib
+        c._scheme, c._precision, c._block = self._scheme, self._precision, self._block
+        c.ell, c.P = self.ell, self.P
+        c._h = out
+        c._borrowed = True
+        c._owner = self
+        return c
 
     def _check_out(self, out, n_steps, host_only=False):
         """The C side writes n_steps * M * 3 doubles to `out`: refuse anything else."""

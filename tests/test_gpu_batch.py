@@ -1,6 +1,7 @@
 """Batched uneven scatterers x excitations (paper_2407_03323_gb300.batch): every march
-of the batch ends where the same march run alone ends (bitwise), and the block-size
-tuner returns one of its candidates."""
+of the batch ends where the same march run alone ends (bitwise), with the excitations
+as separate contexts or as right-hand sides of one context per scatterer, and the
+block-size tuner returns one of its candidates."""
 import os
 
 import numpy as np
@@ -20,12 +21,13 @@ def mot():
     return m
 
 
-def test_batch_matches_individual_marches(mot):
+@pytest.mark.parametrize("rhs", [False, True])
+def test_batch_matches_individual_marches(mot, rhs):
     pytest.importorskip("torch")
     from paper_2407_03323_gb300.batch import BlockTuner, run_batched
     inst = wl.batched_instances(n_instances=3, n_rhs=2, seed=7, side_range=(8, 12))
     tuner = BlockTuner("fp32_history", candidates=(4, 8), buckets=(12,))
-    res = run_batched(inst, 96, tuner=tuner, chunk=32, workers=8)
+    res = run_batched(inst, 96, tuner=tuner, chunk=32, workers=8, rhs=rhs)
     assert set(res["blocks"]) <= {4, 8}
     for i, x in enumerate(inst):
         for j, w in enumerate(x["waves"]):

@@ -1,5 +1,6 @@
 """Degenerate grids through the C ABI: grids one voxel thick along some axes (no
-neighbours there, padded lengths 2), and a grid without dielectric (chi = 0
+neighbours there, padded lengths 2), a single voxel (Z_0 a multiple of the identity:
+the Chebyshev interval collapses to one point), and a grid without dielectric (chi = 0
 everywhere: J stays exactly zero, no solve runs)."""
 import os
 
@@ -20,7 +21,7 @@ def mot():
     return m
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 5), (3, 1, 4)])
+@pytest.mark.parametrize("shape", [(1, 1, 5), (3, 1, 4), (1, 1, 1)])
 def test_thin_grids_match_oracle(mot, shape):
     from oracle import excitation, kernel_table, march
     from oracle.spline import num_lags
