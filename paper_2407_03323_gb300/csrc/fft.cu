@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(NT) k_fwd_x(const double* __restrict__ in, int
     constexpr int ld = TB + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stw = reinterpret_cast<C*>(smem_raw);
-    C* b0 = stw + rl.P;
+    C* b0 = stw + tw_entries<C>(rl.P);
     C* b1 = b0 + rl.P * ld;
     const int P = rl.P, Hu = P / 2 + 1;
     const int VP = (V + 1) / 2;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(NT) k_inv_x(const typename CT<R>::c* __restric
     constexpr int ld = TB + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stw = reinterpret_cast<C*>(smem_raw);
-    C* b0 = stw + rl.P;
+    C* b0 = stw + tw_entries<C>(rl.P);
     C* b1 = b0 + rl.P * ld;
     const int P = rl.P, Hu = P / 2 + 1;
     const int VP = (V + 1) / 2;
@@ -199,9 +199,7 @@ __device__ __forceinline__ void x_four_step(C* X, const C* stw, int nvalid) {
         dft_ct<P2, DIR>(x);
         Unroll1<0, P2>::run([&](auto q) {
             constexpr int k2 = decltype(q)::value;
-            C w = stw[(n1 * k2) % P];
-            if (DIR > 0) w.y = -w.y;
-            x[k2] = cmul(x[k2], w);
+            x[k2] = twmul_tab(stw, (n1 * k2) % P, P, DIR, x[k2]);
         });
     }
     __syncthreads();
@@ -237,11 +235,11 @@ __global__ void k_fwd_x4s(const double* __restrict__ in, int U, int V, int W,
     constexpr int P = P1 * P2, Hu = P / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* X = reinterpret_cast<C*>(smem_raw);          // [P][kXLD]
-    C* stw = X + P * kXLD;                          // [P]
+    C* stw = X + P * kXLD;                          // [tw_entries(P)]
     const int VP = (V + 1) / 2;
     const long long npairs = 3LL * W * VP;
     const long long pair0 = (long long)blockIdx.x * kXL;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < tw_entries<C>(P); i += blockDim.x) stw[i] = tw[i];
     // z = a + i b of the two rows of a pair; positions >= U are the zero padding
     for (int it = threadIdx.x; it < kXL * U; it += blockDim.x) {
         const int t = it / U, j = it % U;
@@ -296,7 +294,7 @@ __global__ void k_inv_x4s(const typename CT<R>::c* __restrict__ in, int U, int V
     const int VP = (V + 1) / 2;
     const long long npairs = 3LL * W * VP;
     const long long pair0 = (long long)blockIdx.x * kXL;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < tw_entries<C>(P); i += blockDim.x) stw[i] = tw[i];
     // Z[k] = A[k] + i B[k] and Z[P-k] = conj A[k] + i conj B[k] from the two halves
     for (int it = threadIdx.x; it < kXL * Hu; it += blockDim.x) {
         const int t = it / Hu, k = it % Hu;
@@ -354,7 +352,7 @@ __global__ void __launch_bounds__(NT) k_mid(const typename CT<R>::c* __restrict_
     constexpr int ld = TB + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stw = reinterpret_cast<C*>(smem_raw);
-    C* b0 = stw + rl.P;
+    C* b0 = stw + tw_entries<C>(rl.P);
     C* b1 = b0 + rl.P * ld;
     const int P = rl.P;
     const int ntile = (a.Hu + TB - 1) / TB;
@@ -394,7 +392,7 @@ k_mid4s(const typename CT<R>::c* __restrict__ in, typename CT<R>::c* __restrict_
     constexpr int P = P1 * P2, NL = 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* Y = reinterpret_cast<C*>(smem_raw);          // [P1][P2][NL]
-    C* stw = Y + P * NL;                            // [P] roots exp(-2 pi i k / P)
+    C* stw = Y + P * NL;                            // roots exp(-2 pi i k / P) (tw_entries)
     const int ntile = (a.Hu + NL - 1) / NL;
     const long long o = blockIdx.x / ntile;
     const int ku0 = (int)(blockIdx.x % ntile) * NL;
@@ -403,7 +401,7 @@ k_mid4s(const typename CT<R>::c* __restrict__ in, typename CT<R>::c* __restrict_
     const bool live = ku0 + lane < a.Hu;
     const C* src = in + comp * a.in_c + o2 * a.in_o + ku0 + lane;
     C* dst = out + comp * a.out_c + o2 * a.out_o + ku0 + lane;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < tw_entries<C>(P); i += blockDim.x) stw[i] = tw[i];
     __syncthreads();
     if (warp < P1) {
         const int n1 = warp;
@@ -419,9 +417,7 @@ k_mid4s(const typename CT<R>::c* __restrict__ in, typename CT<R>::c* __restrict_
         dft_ct<P2, DIR>(x);
         Unroll1<0, P2>::run([&](auto q) {
             constexpr int k2 = decltype(q)::value;
-            C w = stw[(n1 * k2) % P];
-            if (DIR > 0) w.y = -w.y;
-            Y[(n1 * P2 + k2) * NL + lane] = cmul(x[k2], w);
+            Y[(n1 * P2 + k2) * NL + lane] = twmul_tab(stw, (n1 * k2) % P, P, DIR, x[k2]);
         });
     }
     __syncthreads();
@@ -456,7 +452,7 @@ template <> const float2* table<float>(const AxisFFT& a) { return a.tw32; }
 
 template <typename R> size_t smem_bytes(int P) {
     typedef typename CT<R>::c C;
-    return sizeof(C) * ((size_t)P + 2 * (size_t)P * (Tile<R>::TB + 1));
+    return sizeof(C) * ((size_t)tw_entries<C>(P) + 2 * (size_t)P * (Tile<R>::TB + 1));
 }
 
 // Dynamic shared memory of a pass kernel.  The limit is a process-wide attribute of
@@ -478,7 +474,7 @@ template <typename R, int P1, int P2>
 void launch_mid4s(const typename CT<R>::c* in, typename CT<R>::c* out,
                   const typename CT<R>::c* tw, const MidArgs& a, int nblocks, cudaStream_t s) {
     typedef typename CT<R>::c C;
-    const size_t sm = sizeof(C) * ((size_t)P1 * P2 * 32 + (size_t)P1 * P2);
+    const size_t sm = sizeof(C) * ((size_t)P1 * P2 * 32 + (size_t)tw_entries<C>(P1 * P2));
     constexpr int threads = 32 * (P1 > P2 ? P1 : P2);
     if (a.dir < 0) {
         set_smem(k_mid4s<R, P1, P2, -1>, sm);
@@ -518,7 +514,9 @@ __global__ void twiddle_kernel(int P, double2* t64, float2* t32) {
     double s, c;
     sincospi(2.0 * (double)k / (double)P, &s, &c);
     t64[k] = make_double2(c, -s);
-    t32[k] = make_float2((float)c, (float)-s);
+    const float2 h = make_float2((float)c, (float)-s);
+    t32[k] = h;                                                   // hi
+    t32[P + k] = make_float2((float)(c - (double)h.x), (float)(-s - (double)h.y));   // lo
 }
 
 }  // namespace
@@ -535,7 +533,7 @@ void fft_plan_axis(AxisFFT& a, int P) {
         while (n % r == 0) { a.rad[a.nrad++] = r; n /= r; }
     if (n != 1) throw MotError{MOT_ERR_ARG, "FFT length has a prime factor above 7"};
     MOT_CUDA_TRY(cudaMalloc(&a.tw64, sizeof(double2) * P));
-    MOT_CUDA_TRY(cudaMalloc(&a.tw32, sizeof(float2) * P));
+    MOT_CUDA_TRY(cudaMalloc(&a.tw32, sizeof(float2) * 2 * P));
     twiddle_kernel<<<(P + 255) / 256, 256>>>(P, a.tw64, a.tw32);
     MOT_LAUNCH_CHECK();
     MOT_CUDA_TRY(cudaDeviceSynchronize());
@@ -554,7 +552,7 @@ void launch_x4s(bool fwd, mot_ctx* c, const double* Jsoa, typename CT<R>::c* spe
                 const double* scale, cudaStream_t s) {
     typedef typename CT<R>::c C;
     constexpr int P = P1 * P2;
-    const size_t sm = sizeof(C) * ((size_t)P * kXLD + P);
+    const size_t sm = sizeof(C) * ((size_t)P * kXLD + tw_entries<C>(P));
     const int threads = 32 * (P1 > P2 ? P1 : P2);
     const long long npairs = 3LL * c->W * ((c->V + 1) / 2);
     const int blocks = (int)((npairs + kXL - 1) / kXL);

@@ -75,12 +75,43 @@ __host__ __device__ __forceinline__ C twiddle_c(C v) {
         return o;
     } else {
         constexpr CTw w = root_of_unity(K, N);
+        constexpr double wim = DIR < 0 ? w.im : -w.im;
         constexpr R wr = (R)w.re;
-        constexpr R wi = (R)(DIR < 0 ? w.im : -w.im);
+        constexpr R wi = (R)wim;
         C o;
-        o.x = v.x * wr - v.y * wi;
-        o.y = v.x * wi + v.y * wr;
+        if constexpr (std::is_same<R, float>::value) {
+            // FP32: the constant as a float pair hi + lo, so that the rounding of the
+            // twiddle itself (a systematic change of the transform) drops to ~2^-48
+            constexpr float wrl = (float)(w.re - (double)wr), wil = (float)(wim - (double)wi);
+            const float tx = v.x * wrl - v.y * wil, ty = v.x * wil + v.y * wrl;
+            o.x = fmaf(v.x, wr, fmaf(-v.y, wi, tx));
+            o.y = fmaf(v.x, wi, fmaf(v.y, wr, ty));
+        } else {
+            o.x = v.x * wr - v.y * wi;
+            o.y = v.x * wi + v.y * wr;
+        }
         return o;
+    }
+}
+
+// A += s cos(2 pi K / N), B += d sin(2 pi K / N) (odd radices, compile-time
+// constants); in FP32 each constant is applied as a float pair hi + lo (see twiddle_c)
+template <typename Rl, int K, int N, typename C>
+__host__ __device__ __forceinline__ void odd_radix_terms(const C& s, const C& d, C& A, C& B) {
+    constexpr CTw w = root_of_unity(K, N);   // cos - i sin
+    constexpr double CS = w.re, SN = -w.im;
+    constexpr Rl cs = (Rl)CS, sn = (Rl)SN;
+    if constexpr (std::is_same<Rl, float>::value) {
+        constexpr float csl = (float)(CS - (double)cs), snl = (float)(SN - (double)sn);
+        A.x = fmaf(s.x, cs, fmaf(s.x, csl, A.x));
+        A.y = fmaf(s.y, cs, fmaf(s.y, csl, A.y));
+        B.x = fmaf(d.x, sn, fmaf(d.x, snl, B.x));
+        B.y = fmaf(d.y, sn, fmaf(d.y, snl, B.y));
+    } else {
+        A.x += s.x * cs;
+        A.y += s.y * cs;
+        B.x += d.x * sn;
+        B.y += d.y * sn;
     }
 }
 
@@ -121,12 +152,7 @@ __host__ __device__ __forceinline__ void dft_ct(C* x) {
             B.x = 0; B.y = 0;
             Unroll1<1, H + 1>::run([&](auto rc) {
                 constexpr int r = decltype(rc)::value;
-                constexpr CTw w = root_of_unity((q * r) % N, N);   // cos - i sin
-                constexpr Rl cs = (Rl)w.re, sn = (Rl)(-w.im);
-                A.x += s[r - 1].x * cs;
-                A.y += s[r - 1].y * cs;
-                B.x += d[r - 1].x * sn;
-                B.y += d[r - 1].y * sn;
+                odd_radix_terms<Rl, (q * r) % N, N>(s[r - 1], d[r - 1], A, B);
             });
             C mB;   // -i B
             mB.x = B.y; mB.y = -B.x;
@@ -166,12 +192,27 @@ __host__ __device__ __forceinline__ void dft_ct(C* x) {
     }
 }
 
-// dir = -1 forward (exp(-i...)), +1 inverse; W(m) = exp(dir 2 pi i m / P) from table
-template <typename C>
-__device__ __forceinline__ C twid(const C* tw, int m, int dir) {
-    C w = tw[m];
+// Twiddle tables: W_P^m = exp(-2 pi i m / P), m < P; the FP32 table holds a second
+// block of P entries, the low parts (W - hi rounded to FP32), so that it has
+// tw_entries(P) = 2P entries.
+template <typename C> __host__ __device__ constexpr int tw_entries(int P) {
+    return std::is_same<C, float2>::value ? 2 * P : P;
+}
+// v * W(m) for dir = -1 (forward), v * conj W(m) for dir = +1, from a table of P
+// (FP64) or 2P (FP32: hi and lo parts, the twiddle applied as their sum) entries
+__device__ __forceinline__ double2 twmul_tab(const double2* tw, int m, int P, int dir, double2 v) {
+    double2 w = tw[m];
     if (dir > 0) w.y = -w.y;
-    return w;
+    return cmul(v, w);
+}
+__device__ __forceinline__ float2 twmul_tab(const float2* tw, int m, int P, int dir, float2 v) {
+    float2 h = tw[m], l = tw[P + m];
+    if (dir > 0) { h.y = -h.y; l.y = -l.y; }
+    const float tx = v.x * l.x - v.y * l.y, ty = v.x * l.y + v.y * l.x;
+    float2 o;
+    o.x = fmaf(v.x, h.x, fmaf(-v.y, h.y, tx));
+    o.y = fmaf(v.x, h.y, fmaf(v.y, h.x, ty));
+    return o;
 }
 
 template <typename C, int R>
@@ -210,12 +251,7 @@ __device__ __forceinline__ void dft_small(C* v, const C* tw, int P, int dir) {
             B.x = 0; B.y = 0;
             Unroll1<1, H + 1>::run([&](auto rc) {
                 constexpr int r = decltype(rc)::value;
-                constexpr CTw w = root_of_unity((q * r) % R, R);   // cos - i sin
-                constexpr Rl cs = (Rl)w.re, sn = (Rl)(-w.im);
-                A.x += s[r - 1].x * cs;
-                A.y += s[r - 1].y * cs;
-                B.x += d[r - 1].x * sn;
-                B.y += d[r - 1].y * sn;
+                odd_radix_terms<Rl, (q * r) % R, R>(s[r - 1], d[r - 1], A, B);
             });
             // forward: out[q] = A - i B, out[R-q] = A + i B ; inverse: swapped
             C mB;   // -i B
@@ -252,7 +288,7 @@ __device__ __forceinline__ void stage(const C* __restrict__ x, C* __restrict__ y
         if (Ns > 1) {
             const int kt = k * tstep;      // r * kt < P
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], twid(tw, r * kt, dir));
+            for (int r = 1; r < R; ++r) v[r] = twmul_tab(tw, r * kt, P, dir, v[r]);
         }
         dft_small<C, R>(v, tw, P, dir);
         const int base = jq * Ns * R + k;
@@ -292,7 +328,7 @@ struct RadixList {
 
 template <typename C>
 __device__ __forceinline__ void load_tw(C* stw, const C* tw, int P) {
-    for (int i = threadIdx.x; i < P; i += blockDim.x) stw[i] = tw[i];
+    for (int i = threadIdx.x; i < tw_entries<C>(P); i += blockDim.x) stw[i] = tw[i];
 }
 
 // Asynchronous global -> shared copy of one complex value (8 or 16 bytes); with

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
     const int P = 2 * a.S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* stw = reinterpret_cast<C*>(smem_raw);
-    C* b0 = stw + P;
+    C* b0 = stw + tw_entries<C>(P);
     C* b1 = b0 + P * ld;
     // block -> (octant row, mirror, ku tile); the four mirrors of a row are adjacent
     const int ut = blockIdx.x % a.ntile;
@@ -457,12 +457,6 @@ __device__ __forceinline__ double2 shfl_c(double2 v, int mask) {
     return v;
 }
 
-template <int DIR, typename C> __device__ __forceinline__ C table_tw(const C* tw, int i) {
-    C w = tw[i];
-    if (DIR > 0) w.y = -w.y;
-    return w;
-}
-
 // cross-thread DIF stage: span LEN = 2 * HT * Q, partner thread t ^ HT
 template <typename C, int Q, int T, int HT, int DIR>
 __device__ __forceinline__ void dif_cross(C* x, const C* __restrict__ tw, int t) {
@@ -474,7 +468,7 @@ __device__ __forceinline__ void dif_cross(C* x, const C* __restrict__ tw, int t)
         const C mine = x[j];
         const C other = shfl_c(mine, HT * (32 / T));
         if (upper) x[j] = cadd(mine, other);
-        else x[j] = cmul(csub(other, mine), table_tw<DIR>(tw, (base + j) * ts));
+        else x[j] = twmul_tab(tw, (base + j) * ts, P, DIR, csub(other, mine));
     });
 }
 
@@ -486,7 +480,7 @@ __device__ __forceinline__ void dit_cross(C* x, const C* __restrict__ tw, int t)
     Unroll<0, Q>::run([&](auto q) {
         constexpr int j = decltype(q)::value;
         C send = x[j];
-        if (!upper) send = cmul(send, table_tw<DIR>(tw, (base + j) * ts));
+        if (!upper) send = twmul_tab(tw, (base + j) * ts, P, DIR, send);
         const C recv = shfl_c(send, HT * (32 / T));
         x[j] = upper ? cadd(send, recv) : csub(recv, send);
     });
@@ -547,7 +541,7 @@ template <typename R, int Q, int T> struct FarRegSmem {
     static constexpr int P = Q * T, S = P / 2, NB = 32 / T;
     C X[P][3][NB];          // forward spectra of the three components
     C H[S + 1][6][NB];      // the block's level spectra, w = 0..S
-    C tw[P];                // roots of unity for the cross-thread stages
+    C tw[tw_entries<C>(P)]; // roots of unity for the cross-thread stages (FP32: hi, lo)
     int in[P];              // ring slot of every window time (-1: none)
     int out[S];             // accumulator slot of every output time
 };
@@ -592,9 +586,9 @@ __global__ void __launch_bounds__(96) k_far_reg(FarArgs<R> a) {
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
         const int time = a.n0 - P + i;
         sm.in[i] = time >= tfirst ? time % a.hring : -1;
-        sm.tw[i] = a.tw[i];
         if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
     }
+    for (int i = threadIdx.x; i < tw_entries<C>(P); i += blockDim.x) sm.tw[i] = a.tw[i];
     __syncthreads();
     const R sig = comp == 0 ? (R)1 : (comp == 1 ? (fv ? (R)-1 : (R)1) : (fw ? (R)-1 : (R)1));
     C x[Q];
@@ -698,6 +692,7 @@ template <typename R, int P> struct Far4 {
 
 template <typename R, int P>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_far_4s(FarArgs<R> a) {
+    static_assert(std::is_same<R, double>::value, "FP32 far levels run k_far_fs");
     typedef Far4<R, P> F;
     typedef typename F::C C;
     constexpr int Q1 = F::Q1, T = F::T, NB = F::NB, S = F::S;
@@ -843,7 +838,7 @@ void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
     typedef typename CT<R>::c C;
     a.ntile = (c->Hu + TB - 1) / TB;
     const int P = 2 * a.S;
-    const size_t sm = sizeof(C) * ((size_t)P + 2 * (size_t)P * (3 * TB + 1));
+    const size_t sm = sizeof(C) * ((size_t)tw_entries<C>(P) + 2 * (size_t)P * (3 * TB + 1));
     if (sm > 220 * 1024 || a.S > kMaxLevel)
         throw MotError{MOT_ERR_ARG, "blocked scheme: level too long for shared memory"};
     // the limit is process-wide and P varies by level and context: set the device's
@@ -900,7 +895,7 @@ template <int P> struct FarFS {
     struct Smem {
         float2 V[T > 1 ? 3 * CS : 2];
         float2 H[HS];
-        float2 tw[P];          // W_P^m, m < P
+        float2 tw[2 * P];      // W_P^m, m < P, rounded to FP32, then the low parts
         int in[P];             // ring slot of every window time (-1: none)
         int out[S];            // accumulator slot of every output time
     };
@@ -936,6 +931,7 @@ __global__ void __launch_bounds__(128, P <= 16 ? 4 : 2) k_far_fs(FarArgs<float> 
         const int time = a.n0 - P + i;
         sm.in[i] = time >= tfirst ? time % a.hring : -1;
         sm.tw[i] = a.tw[i];
+        sm.tw[P + i] = a.tw[P + i];
         if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
     }
     __syncthreads();
@@ -1019,11 +1015,10 @@ __global__ void __launch_bounds__(128, P <= 16 ? 4 : 2) k_far_fs(FarArgs<float> 
             // ---- phase A (the DFTs over n2 above), twiddles W_P^{t k2}, exchange
             Unroll<0, Q1>::run([&](auto q) {
                 constexpr int k2 = decltype(q)::value;
-                const float2 w = sm.tw[t * k2];
                 float2* dst = &sm.V[k2 * F::KS + t * NB + bin];
-                dst[0] = cmul(x[0][k2], w);
-                dst[F::CS] = cmul(x[1][k2], w);
-                dst[2 * F::CS] = cmul(x[2][k2], w);
+                dst[0] = twmul_tab(sm.tw, t * k2, P, -1, x[0][k2]);
+                dst[F::CS] = twmul_tab(sm.tw, t * k2, P, -1, x[1][k2]);
+                dst[2 * F::CS] = twmul_tab(sm.tw, t * k2, P, -1, x[2][k2]);
             });
             if (mirror == 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
             __syncthreads();
@@ -1060,11 +1055,10 @@ __global__ void __launch_bounds__(128, P <= 16 ? 4 : 2) k_far_fs(FarArgs<float> 
                 Unroll<0, 3>::run([&](auto cq) { dft_ct<T, +1>(v[decltype(cq)::value]); });
                 Unroll<0, T>::run([&](auto q) {
                     constexpr int tt = decltype(q)::value;
-                    const float2 w = cconj(sm.tw[tt * k2]);
                     float2* dst = &sm.V[k2 * F::KS + tt * NB + bin];
-                    dst[0] = cmul(v[0][tt], w);
-                    dst[F::CS] = cmul(v[1][tt], w);
-                    dst[2 * F::CS] = cmul(v[2][tt], w);
+                    dst[0] = twmul_tab(sm.tw, tt * k2, P, +1, v[0][tt]);
+                    dst[F::CS] = twmul_tab(sm.tw, tt * k2, P, +1, v[1][tt]);
+                    dst[2 * F::CS] = twmul_tab(sm.tw, tt * k2, P, +1, v[2][tt]);
                 });
             }
             __syncthreads();

@@ -52,7 +52,8 @@ struct AxisFFT {
     int nrad = 0;
     int rad[16] = {0};
     double2* tw64 = nullptr;  // exp(-2 pi i k / P), k < P (device)
-    float2* tw32 = nullptr;
+    float2* tw32 = nullptr;   // the same rounded to FP32 (k < P), then the low parts
+                              // exp(..) - hi rounded to FP32 (P + k): 2P entries
 };
 
 // Device-side precision-dependent buffers.
