@@ -459,8 +459,8 @@ def oracle_sample(steps, warmup):
 
 def run_batched_bench(args, world):
     """Config of uneven scatterers x excitations (workloads.batched_instances): the
-    marches of every scatterer and excitation, FP32-history, blocked scheme with B
-    tuned per size bucket; a bench step = 128 time steps of every march.  Setup and
+    marches of every scatterer and excitation, FP32-history, blocked scheme with B and
+    the FFT length strategy tuned per size bucket; a bench step = 128 time steps of every march.  Setup and
     tuning (which also warms every kernel variant up) are outside the timed region."""
     import torch
     from paper_2407_03323_gb300.batch import BlockTuner, run_batched
@@ -479,9 +479,10 @@ def run_batched_bench(args, world):
                                    "plane waves, FIR3, %d time steps"
                                    % (len(inst), min(x["N"] for x in inst),
                                       max(x["N"] for x in inst), len(inst[0]["waves"]), n_steps),
-                       "blocks": res["blocks"], "memory_waves": res["waves"],
+                       "blocks": res["blocks"], "fft_lengths": res["fft_lengths"],
+                       "memory_waves": res["waves"],
                        "setup_s": res["setup_s"], "tuning_s_per_step": res["tuning"],
-                       "warmup": "block-size tuning marches of every bucket",
+                       "warmup": "tuning marches (block length x FFT length strategy) of every bucket",
                        "parallelism": "replicas" if world > 1 else "1 GPU"}}
 
 

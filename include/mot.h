@@ -89,6 +89,20 @@ mot_status mot_create(const int grid[3], const double h[3], double dt,
                       int precision, int scheme, int block, mot_ctx** out);
 
 /*
+ * mot_create_padded - mot_create with the zero-padded FFT lengths chosen by the caller
+ * (App. A: any length >= 2 N - 1 per axis makes the circular convolution of the
+ * history equal the linear one, so the march is the same up to rounding): fft_len[a]
+ * for grid axis a (u, v, w), each even, 7-smooth (radices 2, 3, 5, 7), >= 2 grid[a] - 1
+ * and <= 4096; NULL gives mot_create's choice (the smallest such length).  A tuner
+ * picks lengths with a compiled four-step codelet (64, 96, 210) or the smallest one by
+ * timing.  Errors as mot_create (MOT_ERR_ARG for an invalid length).
+ */
+mot_status mot_create_padded(const int grid[3], const double h[3], double dt,
+                             const double* eps_r, const double* fir_taps, int n_taps,
+                             int precision, int scheme, int block, const int fft_len[3],
+                             mot_ctx** out);
+
+/*
  * mot_create_shared - a second, independent marching state on the setup of `src`:
  * the same grid, eps_r, FIR taps, precision, history scheme and solver settings, with
  * the element table, kernel and level spectra, geometry and solver setup shared

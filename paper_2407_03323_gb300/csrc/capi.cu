@@ -158,6 +158,14 @@ extern "C" {
 mot_status mot_create(const int grid[3], const double h[3], double dt, const double* eps_r,
                       const double* fir_taps, int n_taps, int precision, int scheme, int block,
                       mot_ctx** out) {
+    return mot_create_padded(grid, h, dt, eps_r, fir_taps, n_taps, precision, scheme, block,
+                             nullptr, out);
+}
+
+mot_status mot_create_padded(const int grid[3], const double h[3], double dt,
+                             const double* eps_r, const double* fir_taps, int n_taps,
+                             int precision, int scheme, int block, const int fft_len[3],
+                             mot_ctx** out) {
     if (out) *out = nullptr;
     g_create_error.clear();
     auto fail = [](mot_status st, const std::string& m) {
@@ -181,6 +189,12 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         return fail(MOT_ERR_ARG, "unknown history scheme");
     if (scheme == MOT_HISTORY_BLOCKED && (block < 2 || (block & (block - 1)) != 0))
         return fail(MOT_ERR_ARG, "block must be a power of two >= 2 for the blocked scheme");
+    if (fft_len)
+        for (int a = 0; a < 3; ++a)
+            if (fft_len[a] < std::max(2 * grid[a] - 1, 2) || fft_len[a] > 4096 ||
+                fft_len[a] % 2 != 0 || !smooth7(fft_len[a]))
+                return fail(MOT_ERR_ARG, "fft_len[a] must be even, 7-smooth, >= 2 grid[a] - 1 "
+                                         "and <= 4096");
     const long long M = (long long)grid[0] * grid[1] * grid[2];
     for (long long m = 0; m < M; ++m)
         if (!(eps_r[m] >= 1.0) || !std::isfinite(eps_r[m]))
@@ -211,7 +225,8 @@ mot_status mot_create(const int grid[3], const double h[3], double dt, const dou
         mot::excitation_setup(dev);
         MOT_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         const int N[3] = {c->U, c->V, c->W};
-        for (int a = 0; a < 3; ++a) mot::fft_plan_axis(c->ax[a], pad_size(N[a]));
+        for (int a = 0; a < 3; ++a)
+            mot::fft_plan_axis(c->ax[a], fft_len ? fft_len[a] : pad_size(N[a]));
         c->Hu = c->ax[0].P / 2 + 1;
         c->Hv = c->ax[1].P / 2 + 1;
         c->Hw = c->ax[2].P / 2 + 1;

@@ -35,7 +35,8 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
            "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
            "mot_probe_transpose", "mot_barrier_check", "mot_set_graph",
-           "mot_set_excitation_rhs", "mot_march_rhs", "mot_rhs_context", "mot_last_error"]
+           "mot_set_excitation_rhs", "mot_march_rhs", "mot_rhs_context", "mot_create_padded",
+           "mot_last_error"]
 MOT_PDSA_FP32_SPECTRUM = 1
 MOT_PDSA_FULL_REORTH = 2
 
@@ -104,6 +105,7 @@ def load_library(path=LIB_PATH):
     lib.mot_barrier_check.argtypes = [I, I, I, D, P, P]
     lib.mot_set_graph.argtypes = [P, I]
     lib.mot_set_excitation_rhs.argtypes = [P, I, I, P, P]
+    lib.mot_create_padded.argtypes = [P, P, D, P, P, I, I, I, I, P, P]
     lib.mot_march_rhs.argtypes = [P, I, P, P]
     lib.mot_rhs_context.argtypes = [P, I, P]
     lib.mot_last_error.argtypes = [P]
@@ -198,6 +200,36 @@ def fma_peak(fp64=True, target_ms=100.0):
     return fl.value / (ms.value * 1e-3)
 
 
+# FFT lengths with a compiled four-step codelet for the x, y and z passes
+CODELET_LENGTHS = (64, 96, 210)
+
+
+def smooth7(n):
+    for r in (2, 3, 5, 7):
+        while n % r == 0:
+            n //= r
+    return n == 1
+
+
+def pad_size(N):
+    """The library's default zero-padded FFT length for N voxels along an axis: the
+    smallest even 7-smooth length >= 2 N - 1 (App. A)."""
+    P = max(2 * N - 1, 2)
+    while P % 2 or not smooth7(P):
+        P += 1
+    return P
+
+
+def codelet_size(N, limit=1.5):
+    """The smallest codelet length >= 2 N - 1 if it is at most `limit` times pad_size(N),
+    else pad_size(N)."""
+    p = pad_size(N)
+    for c in CODELET_LENGTHS:
+        if c >= 2 * N - 1 and c <= limit * p:
+            return c
+    return p
+
+
 def barrier_check(n_blocks, rounds, absent=-1, budget_s=0.2):
     """One cooperative launch of the solve's grid barrier (mot_barrier_check): returns
     (status, blocks that passed every round, round of a timeout or 0)."""
@@ -212,7 +244,8 @@ def barrier_check(n_blocks, rounds, absent=-1, budget_s=0.2):
 class Context:
     """A marching context (mot_create ... mot_destroy)."""
 
-    def __init__(self, eps_r, taps=None, precision="fp64", scheme="direct", block=0, h=1.0):
+    def __init__(self, eps_r, taps=None, precision="fp64", scheme="direct", block=0, h=1.0,
+                 fft_len=None):
         lib = load_library()
         eps = np.ascontiguousarray(np.asarray(eps_r, dtype=np.float64))
         if eps.ndim != 3:
@@ -224,10 +257,13 @@ class Context:
         hh = (ctypes.c_double * 3)(h, h, h)
         t = np.ascontiguousarray(np.zeros(0) if taps is None else np.asarray(taps, np.float64))
         out = ctypes.c_void_p()
-        st = lib.mot_create(ctypes.cast(grid, ctypes.c_void_p), ctypes.cast(hh, ctypes.c_void_p),
-                            h, eps.ctypes.data, t.ctypes.data if t.size else None, int(t.size),
-                            PRECISIONS[precision], SCHEMES[scheme], int(block),
-                            ctypes.byref(out))
+        fl = None if fft_len is None else (ctypes.c_int * 3)(*[int(v) for v in fft_len])
+        st = lib.mot_create_padded(ctypes.cast(grid, ctypes.c_void_p),
+                                   ctypes.cast(hh, ctypes.c_void_p), h, eps.ctypes.data,
+                                   t.ctypes.data if t.size else None, int(t.size),
+                                   PRECISIONS[precision], SCHEMES[scheme], int(block),
+                                   None if fl is None else ctypes.cast(fl, ctypes.c_void_p),
+                                   ctypes.byref(out))
         if st != MOT_OK:
             raise MotError(st, lib.mot_last_error(None).decode())
         self._h = out

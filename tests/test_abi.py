@@ -103,3 +103,35 @@ def test_barrier_check_rejects_bad_arguments_on_the_host(lib):
     for args in ((4, 0, -1, 0.2), (4, 10, 4, 0.2), (4, 10, -2, 0.2), (4, 10, -1, 0.0),
                  (4, 10, -1, 11.0)):
         assert lib.mot_barrier_check(*args, ctypes.byref(a), ctypes.byref(b)) == 1, args
+
+
+def test_create_padded_rejects_bad_lengths_on_the_host(lib):
+    """mot_create_padded checks every FFT length (even, 7-smooth, >= 2N - 1, <= 4096)
+    before any CUDA call."""
+    out = ctypes.c_void_p()
+    eps = (ctypes.c_double * 64)(*([2.0] * 64))
+    grid = (ctypes.c_int * 3)(4, 4, 4)
+    h = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    for bad in ((6, 8, 8), (8, 8, 9), (22, 8, 8), (8, 8, 4098)):
+        fl = (ctypes.c_int * 3)(*bad)
+        st = lib.mot_create_padded(ctypes.cast(grid, ctypes.c_void_p),
+                                   ctypes.cast(h, ctypes.c_void_p), 1.0,
+                                   ctypes.cast(eps, ctypes.c_void_p), None, 0, 0, 0, 0,
+                                   ctypes.cast(fl, ctypes.c_void_p), ctypes.byref(out))
+        assert st == 1 and not out.value, bad
+        assert b"fft_len" in lib.mot_last_error(None)
+
+
+def test_padding_rules():
+    """The host mirror of the library's padding (smallest even 7-smooth length >= 2N - 1)
+    and the codelet alternative the tuner may choose."""
+    from paper_2407_03323_gb300 import mot
+    from paper_2407_03323_gb300.batch import fft_lengths
+    for N in range(1, 130):
+        P = mot.pad_size(N)
+        assert P >= 2 * N - 1 and P % 2 == 0 and mot.smooth7(P)
+        assert all(q % 2 or not mot.smooth7(q) for q in range(max(2 * N - 1, 2), P))
+        C = mot.codelet_size(N)
+        assert C >= 2 * N - 1 and (C == P or (C in mot.CODELET_LENGTHS and C <= 1.5 * P))
+    assert fft_lengths(24, "pad") == (48, 48, 48) and fft_lengths(24, "codelet") == (64,) * 3
+    assert fft_lengths(40, "codelet") == (96,) * 3 and fft_lengths(104, "pad") == (210,) * 3
