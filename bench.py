@@ -339,10 +339,12 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
     name, b_launch, ms_launch, _ = max(cands, key=lambda x: x[3])
     achieved = b_launch / (ms_launch * 1e-3) / 1e9
     hist_ms = st["ms_fft_fwd"] + st["ms_far"] + st["ms_mac"] + st["ms_fft_inv"]
+    traffic = profile_traffic(args.config, prec, scheme, name)
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_kind": peak_kind,
-            "traffic": profile_traffic(args.config, prec, scheme, name),
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
             "algorithmic_bytes_per_launch": b_launch}
+    if traffic:   # the same fraction from the profiled DRAM bytes instead of the model
+        roof["frac_from_traffic"] = traffic / (ms_launch * 1e-3) / 1e9 / peak
     if prec == "fp64" and peaks:
         # FP64 kernels are bound by FP64 arithmetic here: report against the FP64 rate
         if name == "k_far":
