@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
     int slot = slot_first;
     const R2* gp = reinterpret_cast<const R2*>(ghat + o * 6);
     const long long gstep = g.noct * 3;   // in R2 units per lag
-#pragma unroll 2
+#pragma unroll 8
     for (int l = 1; l <= L; ++l) {
         const R2 g01 = gp[0], g23 = gp[1], g45 = gp[2];
         gp += gstep;
