@@ -329,6 +329,7 @@ class Context:
         if not _dtype_ok(E):
             raise TypeError("E must be float64")
         n = E.shape[0]
+        self._check_out(E, n)
         self._check(self._lib.mot_set_excitation(self._h, n, _ptr(E), _stream(stream)))
 
     def set_excitation_rhs(self, E, stream=None):
@@ -337,6 +338,7 @@ class Context:
         if not _dtype_ok(E):
             raise TypeError("E must be float64")
         n_rhs, n = E.shape[0], E.shape[1]
+        self._check_out(E, n, n_rhs=n_rhs)
         self._check(self._lib.mot_set_excitation_rhs(self._h, n_rhs, n, _ptr(E), _stream(stream)))
         self._n_rhs = n_rhs
 
@@ -346,8 +348,8 @@ class Context:
         n_rhs = getattr(self, "_n_rhs", 1)
         if isinstance(out, str):
             out = np.zeros((n_rhs, n_steps, self.M, 3))
-        if out is not None and not _dtype_ok(out):
-            raise TypeError("out must be float64")
+        if out is not None:
+            self._check_out(out, n_steps, n_rhs=n_rhs)
         self._check(self._lib.mot_march_rhs(self._h, n_steps, _ptr(out), _stream(stream)))
         return out
 
@@ -367,8 +369,9 @@ class Context:
         c._owner = self
         return c
 
-    def _check_out(self, out, n_steps, host_only=False):
-        """The C side writes n_steps * M * 3 doubles to `out`: refuse anything else."""
+    def _check_out(self, out, n_steps, host_only=False, n_rhs=1):
+        """The C side reads or writes n_rhs * n_steps * M * 3 doubles at `out`: refuse
+        anything else."""
         is_np = isinstance(out, np.ndarray)
         if host_only and not (is_np or (hasattr(out, "device") and
                                         str(getattr(out, "device")) == "cpu")):
@@ -378,9 +381,9 @@ class Context:
         if not _dtype_ok(out) or getattr(out, "dtype", None) is None:
             raise TypeError("out must be float64")
         size = out.size if is_np else out.numel()
-        if size != n_steps * self.M * 3:
-            raise ValueError("out holds %d values, %d needed ([n_steps][M][3])"
-                             % (size, n_steps * self.M * 3))
+        if size != n_rhs * n_steps * self.M * 3:
+            raise ValueError("buffer holds %d values, %d needed ([%sn_steps][M][3])"
+                             % (size, n_rhs * n_steps * self.M * 3, "n_rhs][" if n_rhs > 1 else ""))
         contiguous = out.flags["C_CONTIGUOUS"] if is_np else out.is_contiguous()
         if not contiguous:
             raise ValueError("out must be C-contiguous")
@@ -416,8 +419,8 @@ class Context:
         device, or pass a preallocated numpy array / torch tensor."""
         if isinstance(out, str):
             out = np.zeros((n_steps, self.M, 3))
-        if out is not None and not _dtype_ok(out):
-            raise TypeError("out must be float64")
+        if out is not None:
+            self._check_out(out, n_steps)
         self._check(self._lib.mot_march(self._h, n_steps, _ptr(out), _stream(stream)))
         return out
 

@@ -68,6 +68,15 @@ def test_bad_arguments(mot):
         with pytest.raises(mot.MotError) as ei:
             ctx.march(0)
         assert ei.value.status == mot.MOT_ERR_ARG
+        # buffers the library would read or write past their end are refused in Python
+        with pytest.raises(ValueError):
+            ctx.march(4, out=np.zeros((3, 64, 3)))
+        with pytest.raises(TypeError):
+            ctx.set_excitation(np.zeros((4, 64, 3), dtype=np.float32))
+        with pytest.raises(ValueError):
+            ctx.set_excitation(np.zeros((4, 64, 3))[:, ::2])
+        with pytest.raises(ValueError):
+            ctx.set_excitation_rhs(np.zeros((2, 4, 60, 3)))
         with pytest.raises(mot.MotError) as ei:
             ctx.eval_history(np.zeros((ctx.ell + 1, 64, 3)))
         assert ei.value.status == mot.MOT_ERR_ARG
