@@ -446,7 +446,8 @@ typedef struct {
  *   side's status (mot_last_error names it); each one's monitor state is its own
  *   (mot_rhs_context + mot_get_info).  Graph-captured periods are not used here.
  * mot_rhs_context - the context of right-hand side k (k = 0: ctx itself), owned by ctx,
- *   for per-right-hand-side queries (mot_get_info, mot_get_stats, mot_restart ...).
+ *   for per-right-hand-side queries (mot_get_info, mot_get_stats, mot_restart ...);
+ *   mot_destroy on it does nothing (it is destroyed with ctx).
  *   Errors: MOT_ERR_ARG (k outside 0..n_rhs - 1).
  * mot_set_solver on ctx applies to all its right-hand sides.
  */

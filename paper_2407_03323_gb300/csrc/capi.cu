@@ -355,7 +355,7 @@ mot_status mot_create_padded(const int grid[3], const double h[3], double dt,
 }
 
 void mot_destroy(mot_ctx* c) {
-    if (!c) return;
+    if (!c || c->rhs_owner) return;   // a right-hand side goes with the context owning it
     cudaDeviceSynchronize();
     for (mot_ctx* r : c->rhs_ctx) {   // they borrow this context's setup
         free_all(r);
@@ -1069,6 +1069,7 @@ mot_status mot_set_excitation_rhs(mot_ctx* c, int n_rhs, int n_steps, const doub
             }
             r->max_iter = c->max_iter; r->tol = c->tol; r->growth = c->growth;
             r->graph_steps = c->graph_steps;
+            r->rhs_owner = c;
             c->rhs_ctx.push_back(r);
         }
     }
@@ -1120,6 +1121,11 @@ mot_status mot_march_rhs(mot_ctx* c, int n_steps, double* J_out, void* stream) {
         for (int i = 0; i < n_steps; ++i)
             for (MarchRun& r : runs) r.launch_step(i);
     });
+    if (st != MOT_OK) {   // a launch failed: the right-hand sides' states are not read
+        for (mot_ctx* r : all) cudaStreamSynchronize(r->stream);
+        cudaGetLastError();
+        return st;
+    }
     mot_status result = st;
     for (size_t k = 0; k < runs.size(); ++k) {
         const mot_status sk = guarded(all[k], [&] { runs[k].fetch(); });

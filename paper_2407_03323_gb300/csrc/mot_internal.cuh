@@ -181,6 +181,7 @@ struct mot_ctx {
     int device = 0;              // CUDA device the context was created on
     std::vector<mot_ctx*> rhs_ctx;   // further right-hand sides (mot_set_excitation_rhs):
                                      // contexts sharing this one's setup, owned by it
+    mot_ctx* rhs_owner = nullptr;    // for such a right-hand side: the owning context
     int graph_steps = 0;         // steps per CUDA graph of the march (0: no graphs)
     cudaGraphExec_t gexec = nullptr;   // executable graph of one period, updated in place
 
