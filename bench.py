@@ -6,10 +6,11 @@ FIR3 regularisation (Eq. FIR3) with delta = 1e-7 * 104^3, single x-polarised +z
 modulated-Gaussian plane wave (the pulse peaks inside the timed window).
 
 Variants: FP32-history and FP64 with the blocked temporal scheme (block B = 8, levels
-8..128), and the plain FP64 direct march for comparison.  A bench "step" is one pass
-of every row of the hot path: for the blocked scheme one period of the block schedule
-(S_max = 128 time steps, in which every level fires), for the direct scheme one time
-step.  Each time step runs the forward FFT of J_{n-1}, the far-lag block products due
+of length 8, 16, 32, 64 over lags [S, 2S) and one of length 64 over lags 128..191,
+the last fitted to ell = 182), and the plain FP64 direct march for comparison.  A bench
+"step" is one pass of every row of the hot path: for the blocked scheme 128 time steps
+(two periods of the block schedule, in each of which every level fires), for the
+direct scheme one time step.  Each time step runs the forward FFT of J_{n-1}, the far-lag block products due
 at that step, the near-lag MAC, the inverse FFT, the FIR epilogue and the Z_0 solve.
 
 Metric: voxel-timesteps/s = (bounding-grid voxels) x (time steps) / march time.
@@ -54,7 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="both", choices=["both", "fp32_history", "fp64"])
     ap.add_argument("--config", default=CONFIG_NAME)
-    ap.add_argument("--scheme", default="blocked", choices=["blocked", "direct"])
+    ap.add_argument("--scheme", default="blocked",
+                    choices=["blocked", "blocked_doubling", "direct"])
     ap.add_argument("--block", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -151,21 +153,23 @@ def mac_bytes_per_launch(ctx, precision, lags, n_levels):
 
 def far_bytes_per_period(ctx, precision):
     """Algorithmic bytes of every block Toeplitz launch of one period (each level S
-    fires S_max / S times): the window of min(2S - 1, ell) past spectra (3 complex per
-    bin), the level's temporal kernel spectra (S + 1 frequencies x 6 complex per
-    octant bin), and the S future accumulators it writes (3 complex per bin)."""
+    fires period / S times): the past spectra of its window that some output uses
+    (lags a .. a + S - 1 of outputs n0 .. n0 + S - 1 reach back to n0 - a - S + 1, and
+    nothing older than n0 - ell is used: min(2S - 1, ell - a + S) times, 3 complex per
+    bin), the level's temporal kernel spectra (S + 1 frequencies x 6 complex per octant
+    bin), and the S future accumulators it writes (3 complex per bin)."""
     c = 16 if precision == "fp64" else 8
     noct, nbins = geometry(ctx)
-    levels = ctx.levels
+    levels, lags = ctx.levels, ctx.level_lags
     if not levels:
         return 0, 0
-    smax = levels[-1]
+    period = max(levels)
     total, launches = 0, 0
-    for S in levels:
-        lmax = min(2 * S - 1, ctx.ell)
-        per = 3 * c * nbins * lmax + (S + 1) * 6 * c * noct + S * 3 * c * nbins
-        total += per * (smax // S)
-        launches += smax // S
+    for S, a in zip(levels, lags):
+        live = min(2 * S - 1, ctx.ell - a + S)
+        per = 3 * c * nbins * live + (S + 1) * 6 * c * noct + S * 3 * c * nbins
+        total += per * (period // S)
+        launches += period // S
     return total, launches
 
 
@@ -179,13 +183,13 @@ def far_flops_per_period(ctx):
     levels = ctx.levels
     if not levels:
         return 0, 0
-    smax = levels[-1]
+    period = max(levels)
     total, launches = 0.0, 0
     for S in levels:
         n = 2 * S
         per = nbins * (2 * 3 * 5 * n * math.log2(n) + 72 * n)
-        total += per * (smax // S)
-        launches += smax // S
+        total += per * (period // S)
+        launches += period // S
     return total, launches
 
 
@@ -303,8 +307,9 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
     ctx = Context(eps, taps, precision=prec, scheme=scheme, block=block)
     setup_s = time.time() - t_setup
     stream = torch.cuda.current_stream()
-    # a bench step: one time step (direct), one period of the block schedule (blocked)
-    per = ctx.levels[-1] if (scheme == "blocked" and ctx.levels) else 1
+    # a bench step: one time step (direct); 128 time steps, whole periods of the block
+    # schedule (every level fires in each), for the blocked scheme
+    per = ctx.period * max(1, 128 // ctx.period) if scheme.startswith("blocked") else 1
     n_warm, n_time = warmup * per, steps * per
     # warm-up marches the pulse's leading edge; the timed steps get the pulse itself
     Ew = torch.zeros((min(n_warm, per), M, 3), dtype=torch.float64, device="cuda")
@@ -325,12 +330,12 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
     info = ctx.info()
     peak, peak_kind = measured_peaks()
     # dominant kernel of the history evaluation
-    mac_lags = min(block - 1, ctx.ell) if scheme == "blocked" else ctx.ell
+    mac_lags = min(block - 1, ctx.ell) if scheme.startswith("blocked") else ctx.ell
     mac_b = mac_bytes_per_launch(ctx, prec, mac_lags,
-                                 len(ctx.levels) if scheme == "blocked" else 0)
+                                 len(ctx.levels) if scheme.startswith("blocked") else 0)
     mac_ms = st["ms_mac"] / max(st["mac_launches"], 1)
     cands = [("k_mac", mac_b, mac_ms, st["ms_mac"])]
-    if scheme == "blocked" and st["far_launches"]:
+    if scheme.startswith("blocked") and st["far_launches"]:
         fb, fl = far_bytes_per_period(ctx, prec)
         periods = st["far_launches"] / max(fl, 1)
         far_bytes_launch = fb / max(fl, 1)
@@ -362,7 +367,7 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
                 "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "peak_kind": peak_kind}}
     out = {
-        "scheme": scheme, "block": block if scheme == "blocked" else None,
+        "scheme": scheme, "block": block if scheme.startswith("blocked") else None,
         "time_steps_per_bench_step": per,
         "value": job_throughput(M * n_time, ms * 1e-3, world),
         "ms_per_step": ms / steps, "ms_per_time_step": ms / n_time,
@@ -373,6 +378,7 @@ def run_variant(args, cfg, prec, scheme, block, dev, world, steps, warmup, want_
         "history_ms_per_time_step": hist_ms / max(st["steps"], 1),
         "roofline": roof,
         "clocks": clocks, "ell": info["ell"], "P": list(info["P"]), "levels": ctx.levels,
+        "level_lags": ctx.level_lags,
     }
     W_, V_, U_ = eps.shape
     out["fft_comparison"] = {
@@ -415,14 +421,14 @@ def run_ours(args, rank, world):
     precs = ["fp32_history", "fp64"] if args.precision == "both" else [args.precision]
     for prec in precs:
         variants.append((prec, args.scheme, args.block))
-    if args.precision == "both" and args.scheme == "blocked":
+    if args.precision == "both" and args.scheme.startswith("blocked"):
         variants.append(("fp64", "direct", 0))     # the plain FP64 march, for comparison
     results, e2e = {}, None
     peaks = fma_peaks() if any(v[0] == "fp64" for v in variants) else None
     for prec, scheme, block in variants:
         # the plain direct FP64 march is slow: time a few single steps
         steps, warm = (args.steps, args.warmup)
-        if scheme == "direct" and args.scheme == "blocked":
+        if scheme == "direct" and args.scheme.startswith("blocked"):
             steps, warm = 8, 3
         r, e = run_variant(args, cfg, prec, scheme, block, dev, world, steps, warm,
                            want_e2e=(e2e is None and not args.no_e2e), peaks=peaks)
@@ -536,10 +542,11 @@ def main():
                                "delta=1e-7*M, +z x-polarised modulated Gaussian plane wave"
                                % (round(M ** (1 / 3)), M),
                    "variant": head_key,
-                   "step": ("one period of the block schedule = %d time steps"
+                   "step": ("%d time steps (whole periods of the block schedule)"
                             % head["time_steps_per_bench_step"])
                            if head["time_steps_per_bench_step"] > 1 else "one time step",
-                   "levels": head["levels"], "P": head["P"], "ell": head["ell"],
+                   "levels": head["levels"], "level_lags": head["level_lags"],
+                   "P": head["P"], "ell": head["ell"],
                    "l2_flush": "inputs larger than L2 (spectral ring)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": head["roofline"],

@@ -23,7 +23,8 @@
  *  - Every call returns a mot_status.  On error, mot_last_error(ctx) returns a
  *    message.  A context stays usable after MOT_ERR_ARG / MOT_ERR_NOT_CONVERGED /
  *    MOT_ERR_UNSTABLE; after MOT_ERR_CUDA or MOT_ERR_TIMEOUT it is in
- *    MOT_ERR_STATE and only mot_last_error / mot_get_info / mot_destroy work.
+ *    MOT_ERR_STATE and only mot_last_error / mot_get_info / mot_get_levels /
+ *    mot_destroy work.
  *  - Calls on one context are not thread safe; separate contexts are independent.
  */
 #ifndef MOT_H
@@ -57,8 +58,14 @@ typedef enum {
 typedef enum {
     MOT_HISTORY_DIRECT = 0,  /* every lag 1..ell multiplied per step in the spatial
                                 spectral domain (Sec. 3, Eq. PnFFTMOT)                */
-    MOT_HISTORY_BLOCKED = 1  /* lags >= B by block Toeplitz products with temporal
-                                FFTs (Secs. 4-5); lags < B as in DIRECT               */
+    MOT_HISTORY_BLOCKED = 1, /* lags >= B by block Toeplitz products with temporal
+                                FFTs (Secs. 4-5); lags < B as in DIRECT.  Levels of
+                                length S = B, 2B, ... over lags [S, 2S); where at
+                                most half of the last one's lags [a, 2a) are <= ell,
+                                it is replaced by the shortest level S' = B 2^j over
+                                lags [a, a + S') that reaches ell; mot_get_levels   */
+    MOT_HISTORY_BLOCKED_DOUBLING = 2  /* the blocked scheme with every level over
+                                [S, 2S), the last one included                       */
 } mot_history_scheme;
 
 /*
@@ -79,7 +86,7 @@ typedef enum {
  *            may be NULL when n_taps = 0; copied
  *  precision mot_precision
  *  scheme    mot_history_scheme
- *  block     block size B for MOT_HISTORY_BLOCKED (power of two, 2..ell), else 0
+ *  block     block size B for the blocked schemes (power of two, 2..ell), else 0
  *  out       receives the context (NULL on failure)
  * Errors: MOT_ERR_ARG, MOT_ERR_OOM, MOT_ERR_CUDA.  On failure *out is NULL and the
  * message is available from mot_last_error(NULL).
@@ -395,6 +402,21 @@ mot_status mot_frequency_response(int n_steps, int n_probe, const double* J, dou
 mot_status mot_get_info(const mot_ctx* ctx, int* ell, int P[3], int* n_done,
                         double* last_norm, int* fail_step, int* last_cg_iters);
 
+/*
+ * mot_get_levels - the far levels of the blocked schemes (Secs. 4-5): level k has
+ * length S[k] (it fires at every step n with (n - 1) mod S[k] = 0, a temporal FFT of
+ * length 2 S[k]) and covers lags lag0[k] .. lag0[k] + S[k] - 1; lags 1 .. B - 1 are
+ * the near lags.  The firing pattern repeats every max S[k] steps (the period that
+ * mot_set_graph requires).
+ *  max_levels  capacity of S and lag0 (at most 8 levels exist)
+ *  n_levels    receives the number of levels (0 for MOT_HISTORY_DIRECT)
+ *  S, lag0     host arrays of max_levels ints, or NULL; the first
+ *              min(n_levels, max_levels) entries are written
+ * Errors: MOT_ERR_ARG (ctx or n_levels NULL, max_levels < 0); MOT_ERR_STATE after a
+ * CUDA error (the values are still written).
+ */
+mot_status mot_get_levels(const mot_ctx* ctx, int max_levels, int* n_levels, int* S, int* lag0);
+
 /* Set per-step solver/monitor parameters.  tol: the FP64 residual of the Z_0 solve
  * must fall below tol ||rhs / chi|| (default 1e-13 for MOT_FP64, 3e-8 for
  * MOT_FP32_HISTORY, whose history already carries ~2e-7 relative error); max_iter:
@@ -469,8 +491,8 @@ mot_status mot_rhs_context(mot_ctx* ctx, int k, mot_ctx** out);
  * Used only when the excitation is on the device (or fully staged), J_out is NULL or a
  * device pointer, profiling is off and the stream is not a default stream; otherwise
  * mot_march launches step by step.  Q = 0 turns graphs off.
- * Errors: MOT_ERR_ARG (Q < 0 or Q > 65536; with the blocked scheme Q not a multiple of
- * the longest level's period, see mot_get_info levels).
+ * Errors: MOT_ERR_ARG (Q < 0 or Q > 65536; with a blocked scheme Q not a multiple of
+ * the longest level's length, see mot_get_levels).
  */
 mot_status mot_set_graph(mot_ctx* ctx, int steps_per_graph);
 

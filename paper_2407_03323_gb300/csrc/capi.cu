@@ -185,9 +185,10 @@ mot_status mot_create_padded(const int grid[3], const double h[3], double dt,
         return fail(MOT_ERR_ARG, "n_taps must be 0..64 and fir_taps non-null when n_taps > 0");
     if (precision != MOT_FP64 && precision != MOT_FP32_HISTORY)
         return fail(MOT_ERR_ARG, "unknown precision");
-    if (scheme != MOT_HISTORY_DIRECT && scheme != MOT_HISTORY_BLOCKED)
+    if (scheme != MOT_HISTORY_DIRECT && scheme != MOT_HISTORY_BLOCKED &&
+        scheme != MOT_HISTORY_BLOCKED_DOUBLING)
         return fail(MOT_ERR_ARG, "unknown history scheme");
-    if (scheme == MOT_HISTORY_BLOCKED && (block < 2 || (block & (block - 1)) != 0))
+    if (scheme != MOT_HISTORY_DIRECT && (block < 2 || (block & (block - 1)) != 0))
         return fail(MOT_ERR_ARG, "block must be a power of two >= 2 for the blocked scheme");
     if (fft_len)
         for (int a = 0; a < 3; ++a)
@@ -205,7 +206,9 @@ mot_status mot_create_padded(const int grid[3], const double h[3], double dt,
     c->U = grid[0]; c->V = grid[1]; c->W = grid[2];
     c->M = M;
     c->precision = precision;
-    c->scheme = scheme;
+    // both blocked plans run the same code; they differ in the last level only
+    c->scheme = scheme == MOT_HISTORY_DIRECT ? MOT_HISTORY_DIRECT : MOT_HISTORY_BLOCKED;
+    c->lev_fit = scheme == MOT_HISTORY_BLOCKED;
     c->block = block;
     c->n_taps = n_taps;
     c->taps.assign(fir_taps, fir_taps + n_taps);
@@ -251,7 +254,7 @@ mot_status mot_create_padded(const int grid[3], const double h[3], double dt,
         if (precision == MOT_FP64) alloc_history<double>(c);
         else alloc_history<float>(c);
         mot::compute_spectra(c);
-        if (scheme == MOT_HISTORY_BLOCKED) {
+        if (c->scheme == MOT_HISTORY_BLOCKED) {
             if (precision == MOT_FP64) mot::level_spectra<double>(c);
             else mot::level_spectra<float>(c);
         }
@@ -393,8 +396,10 @@ mot_status mot_create_shared(mot_ctx* src, mot_ctx** out) {
     for (int e = 0; e < 27; ++e) c->noff[e] = src->noff[e];
     c->tab_l0 = src->tab_l0; c->tab = src->tab;
     c->nlev = src->nlev;
+    c->lev_period = src->lev_period;
+    c->lev_fit = src->lev_fit;
     for (int k = 0; k < 8; ++k) {
-        c->lev_S[k] = src->lev_S[k]; c->lev_off[k] = src->lev_off[k];
+        c->lev_S[k] = src->lev_S[k]; c->lev_a[k] = src->lev_a[k]; c->lev_off[k] = src->lev_off[k];
         c->lev_fft[k] = src->lev_fft[k]; c->lev_acc[k] = src->lev_acc[k];
     }
     c->smax = src->smax;
@@ -1014,6 +1019,17 @@ mot_status mot_get_info(const mot_ctx* c, int* ell, int P[3], int* n_done, doubl
     return c->broken ? MOT_ERR_STATE : MOT_OK;
 }
 
+mot_status mot_get_levels(const mot_ctx* c, int max_levels, int* n_levels, int* S, int* lag0) {
+    if (!c || max_levels < 0 || !n_levels) return MOT_ERR_ARG;
+    const int n = c->scheme == MOT_HISTORY_BLOCKED ? c->nlev : 0;
+    *n_levels = n;
+    for (int k = 0; k < n && k < max_levels; ++k) {
+        if (S) S[k] = c->lev_S[k];
+        if (lag0) lag0[k] = c->lev_a[k];
+    }
+    return c->broken ? MOT_ERR_STATE : MOT_OK;
+}
+
 mot_status mot_set_solver(mot_ctx* c, double tol, int max_iter, double growth_limit) {
     if (!c) return MOT_ERR_ARG;
     if (!(tol > 0) || max_iter < 1 || !(growth_limit > 1)) {
@@ -1160,10 +1176,10 @@ mot_status mot_set_graph(mot_ctx* c, int steps_per_graph) {
         return MOT_ERR_ARG;
     }
     if (steps_per_graph > 0 && c->scheme == MOT_HISTORY_BLOCKED && c->nlev > 0 &&
-        steps_per_graph % c->lev_S[c->nlev - 1] != 0) {
+        steps_per_graph % c->lev_period != 0) {
         char b[160];
         snprintf(b, sizeof b, "steps_per_graph must be a multiple of the longest level's "
-                 "period %d", c->lev_S[c->nlev - 1]);
+                 "period %d", c->lev_period);
         c->err = b;
         return MOT_ERR_ARG;
     }

@@ -13,13 +13,16 @@
 // so the accumulation over up to ell lags adds no error beyond one rounding of the
 // compensated total.
 // Blocked temporal scheme (Secs. 4-5, MOT_HISTORY_BLOCKED): lags 1..B-1 are multiplied
-// every step as above; the lags [S, 2S) for S = B, 2B, 4B, ... form level S.  At every
-// step n0 with (n0 - 1) mod S = 0 the level computes its contribution to the next S
-// histories, y(n0 + j) = sum_{l=S}^{2S-1} Ghat_l Jhat(n0 + j - l), j < S, as one block
-// Toeplitz product by overlap-save: per spectral bin a length-2S FFT over time of the
-// window Jhat(n0 - 2S .. n0 - 1) (read from the ring), a product with the precomputed
-// temporal spectrum of [Ghat_S .. Ghat_{2S-1}, 0 .. 0], an inverse FFT, and the last
-// S outputs written to that level's own ring of future-history accumulators (S slots).
+// every step as above; the lags [a, a + S) form a level of length S, with a = S for
+// S = B, 2B, 4B, ... and, where the last of these would reach far past ell, a shorter
+// last level over the remaining lags (history_alloc).  At every step n0 with
+// (n0 - 1) mod S = 0 the level computes its contribution to the next S histories,
+// y(n0 + j) = sum_{l=a}^{a+S-1} Ghat_l Jhat(n0 + j - l), j < S, as one block Toeplitz
+// product by overlap-save: per spectral bin a length-2S FFT over time of the window
+// Jhat(n0 - a - S .. n0 - a + S - 1) (read from the ring; with a >= S all of it lies
+// before n0), a product with the precomputed temporal spectrum of
+// [Ghat_a .. Ghat_{a+S-1}, 0 .. 0], an inverse FFT, and the last S outputs written to
+// that level's own ring of future-history accumulators (S slots).
 // Every time is covered by exactly one firing of each level, so a firing only stores
 // (no read-modify-write), and the per-step near MAC adds every level's entry for its
 // step.  A level's inputs are all older than n0,
@@ -141,11 +144,12 @@ __global__ void __launch_bounds__(NT) k_mac(const R* __restrict__ ghat,
     v = az.get(); v.x *= scale; v.y *= scale; phat[2 * g.nbins + bidx] = v;
 }
 
-// temporal spectra of level S: H(w) = sum_{m=0}^{lmax-S} Ghat_{S+m} exp(-2 pi i w m / (2S)),
+// temporal spectra of the level of length S over lags [a, a + S):
+// H(w) = sum_{m=0}^{lmax-a} Ghat_{a+m} exp(-2 pi i w m / (2S)), lmax = min(a + S - 1, ell),
 // w = 0..S (the rest follows by H(2S - w) = conj H(w)); out [w][6][octant bin], one
 // plane per component so that a warp over consecutive bins reads one contiguous run
 template <typename R>
-__global__ void k_level_spec(const R* __restrict__ ghat, long long noct, int S, int lmax,
+__global__ void k_level_spec(const R* __restrict__ ghat, long long noct, int S, int a, int lmax,
                              const double2* __restrict__ tw, typename CT<R>::c* __restrict__ out) {
     typedef typename CT<R>::c C;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -154,9 +158,9 @@ __global__ void k_level_spec(const R* __restrict__ ghat, long long noct, int S, 
     const int w = (int)(i / noct);
     double2 acc[6];
     for (int c = 0; c < 6; ++c) acc[c] = make_double2(0.0, 0.0);
-    for (int m = 0; m <= lmax - S; ++m) {
+    for (int m = 0; m <= lmax - a; ++m) {
         const double2 t = tw[((long long)w * m) % (2 * S)];
-        const R* gp = ghat + ((long long)(S + m - 1) * noct + o) * 6;
+        const R* gp = ghat + ((long long)(a + m - 1) * noct + o) * 6;
         for (int c = 0; c < 6; ++c) {
             const double g = (double)gp[c];
             acc[c].x += g * t.x;
@@ -183,6 +187,7 @@ template <typename R> struct FarArgs {
     C* acc;              // this level's accumulator ring [smax][3][nbins]
     int smax;            // its length (S)
     int n0, S, lmax;
+    int w0;              // window start n0 - a - S (a the level's first lag): time of x[0]
     int Hu, Hv, Hw, Pv, Pw;
     int ntile;
     RadixList rl;        // length 2S
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(NT) k_far(FarArgs<R> a) {
     __shared__ int s_out[kMaxLevel];
     const int tfirst = max(1, a.n0 - a.lmax);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int time = a.n0 - P + i;
+        const int time = a.w0 + i;
         s_in[i] = time >= tfirst ? time % a.hring : -1;
         if (i < a.S) s_out[i] = (a.n0 + i) % a.smax;
     }
@@ -305,14 +310,33 @@ void history_alloc(mot_ctx* c) {
     MOT_CUDA_TRY(cudaMalloc(&hb.tmp2, sizeof(C) * 3LL * c->W * c->ax[1].P * c->Hu));
     MOT_CUDA_TRY(cudaMalloc(&hb.hist_spatial, sizeof(R) * 3 * c->M));
     if (c->scheme == MOT_HISTORY_BLOCKED) {
+        // doubling levels: lags [S, 2S) for S = B, 2B, ... while S <= ell.  The last of
+        // them may reach far beyond ell (at 104^3, ell = 182: [128, 256) for 55 live
+        // lags).  With lev_fit, when the lags left for it, [a, ell], number at most a / 2,
+        // it becomes the shortest level S' = B 2^j >= ell - a + 1 over [a, a + S'): a
+        // Toeplitz block needs only S' <= a to use computed currents alone, and a level
+        // costs per step about the same bytes whatever S but fewer butterflies for a
+        // shorter transform (the 2S = 256 transform of the example fires for 55 lags)
         c->nlev = 0;
-        long long spec = 0;
         for (int S = c->block; S <= c->ell && c->nlev < 8; S *= 2) {
             c->lev_S[c->nlev] = S;
-            c->lev_off[c->nlev] = spec;
-            spec += (long long)(S + 1) * c->noct * 6;
-            fft_plan_axis(c->lev_fft[c->nlev], 2 * S);
+            c->lev_a[c->nlev] = S;
             ++c->nlev;
+        }
+        if (c->lev_fit && c->nlev >= 2) {
+            const int a = c->lev_a[c->nlev - 1], rest = c->ell - a + 1;
+            int S = c->block;
+            while (S < rest) S *= 2;
+            if (S < c->lev_S[c->nlev - 1]) c->lev_S[c->nlev - 1] = S;
+        }
+        long long spec = 0;
+        c->lev_period = 1;
+        for (int k = 0; k < c->nlev; ++k) {
+            const int S = c->lev_S[k];
+            c->lev_off[k] = spec;
+            spec += (long long)(S + 1) * c->noct * 6;
+            fft_plan_axis(c->lev_fft[k], 2 * S);
+            c->lev_period = std::max(c->lev_period, S);
         }
         // one accumulator ring per level (S slots each): every firing writes its
         // outputs, the near MAC of a step sums the levels' entries for that step
@@ -322,7 +346,7 @@ void history_alloc(mot_ctx* c) {
             acc_slots += c->lev_S[k];
         }
         c->smax = std::max<long long>(acc_slots, 1);
-        if (c->nlev && 2 * c->lev_S[c->nlev - 1] < c->ell + 1)
+        if (c->nlev && c->lev_a[c->nlev - 1] + c->lev_S[c->nlev - 1] < c->ell + 1)
             throw MotError{MOT_ERR_ARG, "blocked scheme: more than 8 levels needed; raise block"};
         MOT_CUDA_TRY(cudaMalloc(&hb.level_spec, sizeof(C) * std::max<long long>(spec, 1)));
         MOT_CUDA_TRY(cudaMalloc(&hb.acc_ring, sizeof(C) * slot * c->smax));
@@ -375,11 +399,11 @@ template <typename R>
 void level_spectra(mot_ctx* c) {
     HistoryBuffers<R>& hb = hbuf<R>(c);
     for (int k = 0; k < c->nlev; ++k) {
-        const int S = c->lev_S[k];
-        const int lmax = std::min(2 * S - 1, c->ell);
+        const int S = c->lev_S[k], a = c->lev_a[k];
+        const int lmax = std::min(a + S - 1, c->ell);
         const long long n = c->noct * (S + 1);
         k_level_spec<R><<<(int)((n + NT - 1) / NT), NT, 0, c->stream>>>(
-            hb.ghat, c->noct, S, lmax, c->lev_fft[k].tw64, hb.level_spec + c->lev_off[k]);
+            hb.ghat, c->noct, S, a, lmax, c->lev_fft[k].tw64, hb.level_spec + c->lev_off[k]);
         MOT_LAUNCH_CHECK();
     }
     MOT_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -584,7 +608,7 @@ __global__ void __launch_bounds__(96) k_far_reg(FarArgs<R> a) {
     }
     const int tfirst = max(1, a.n0 - a.lmax);
     for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        const int time = a.n0 - P + i;
+        const int time = a.w0 + i;
         sm.in[i] = time >= tfirst ? time % a.hring : -1;
         if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
     }
@@ -721,7 +745,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_far_4s(FarArgs<
     }
     const int tfirst = max(1, a.n0 - a.lmax);
     for (int i = tid; i < P; i += F::NTB) {
-        const int time = a.n0 - P + i;
+        const int time = a.w0 + i;
         sm.in[i] = time >= tfirst ? time % a.hring : -1;
         if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
         if (i < Q1) sm.tw[i] = a.tw[i];     // W_P^i
@@ -861,7 +885,7 @@ void far_launch(mot_ctx* c, FarArgs<R>& a, cudaStream_t s) {
 // components of its share of a temporal line: the 3x3 product then needs no exchange
 // between components, and every thread works in every phase.
 //   phase A: thread (t, bin) loads x[t + T n2], n2 < 16, of the three components (the
-//            window times n0 - P + t + T n2; zero before tfirst), runs the 16-point
+//            window times w0 + t + T n2; zero before tfirst), runs the 16-point
 //            DFTs in registers (compile-time twiddles), multiplies by W_P^{t k2} and
 //            stores to shared memory;
 //   phase B: thread (tt, bin) takes k2 = tt, tt + T, ...: the T values of each
@@ -928,7 +952,7 @@ __global__ void __launch_bounds__(128, P <= 16 ? 4 : 2) k_far_fs(FarArgs<float> 
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     }
     for (int i = tid; i < P; i += F::NTH) {
-        const int time = a.n0 - P + i;
+        const int time = a.w0 + i;
         sm.in[i] = time >= tfirst ? time % a.hring : -1;
         sm.tw[i] = a.tw[i];
         if (i < S) sm.out[i] = (a.n0 + i) % a.smax;
@@ -1108,7 +1132,8 @@ void far_level(mot_ctx* c, int k, int n0, cudaStream_t s) {
     a.smax = c->lev_S[k];
     a.n0 = n0;
     a.S = c->lev_S[k];
-    a.lmax = std::min(2 * a.S - 1, c->ell);
+    a.lmax = std::min(c->lev_a[k] + a.S - 1, c->ell);
+    a.w0 = n0 - c->lev_a[k] - a.S;
     a.Hu = c->Hu; a.Hv = c->Hv; a.Hw = c->Hw;
     a.Pv = c->ax[1].P; a.Pw = c->ax[2].P;
     const AxisFFT& f = c->lev_fft[k];

@@ -148,8 +148,11 @@ struct mot_ctx {
 
     HistoryBuffers<double> h64;
     HistoryBuffers<float> h32;
-    int nlev = 0;                // blocked scheme levels S = B, 2B, ...
-    int lev_S[8] = {0};
+    int nlev = 0;                // blocked scheme levels: lags [lev_a, lev_a + lev_S)
+    int lev_S[8] = {0};          // level length S (fires every S steps, transform 2S)
+    int lev_a[8] = {0};          // its first lag (S for the doubling levels B, 2B, ...)
+    int lev_period = 1;          // the longest S: the firing pattern repeats with it
+    bool lev_fit = true;         // last level fitted to ell (MOT_HISTORY_BLOCKED)
     long long lev_off[8] = {0};  // offsets of the level spectra
     AxisFFT lev_fft[8];          // temporal FFT plans of length 2S
     long long lev_acc[8] = {0};  // first accumulator slot of each level's ring

@@ -24,13 +24,14 @@ STATUS_NAMES = {0: "MOT_OK", 1: "MOT_ERR_ARG", 2: "MOT_ERR_OOM", 3: "MOT_ERR_CUD
                 4: "MOT_ERR_NOT_CONVERGED", 5: "MOT_ERR_UNSTABLE", 6: "MOT_ERR_TIMEOUT",
                 7: "MOT_ERR_STATE"}
 PRECISIONS = {"fp64": 0, "fp32_history": 1}
-SCHEMES = {"direct": 0, "blocked": 1}
+SCHEMES = {"direct": 0, "blocked": 1, "blocked_doubling": 2}
 
 EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation",
            "mot_plane_wave",
            "mot_plane_wave_static", "mot_march", "mot_restart", "mot_adjoint_begin",
            "mot_adjoint_run", "mot_adjoint_end",
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
+           "mot_get_levels",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
            "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
@@ -89,6 +90,7 @@ def load_library(path=LIB_PATH):
     lib.mot_get_table.argtypes = [P, I, I, P]
     lib.mot_get_spectrum.argtypes = [P, I, P]
     lib.mot_get_info.argtypes = [P, P, P, P, P, P, P]
+    lib.mot_get_levels.argtypes = [P, I, P, P, P]
     lib.mot_set_solver.argtypes = [P, D, I, D]
     lib.mot_set_profiling.argtypes = [P, I]
     lib.mot_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -572,16 +574,32 @@ class Context:
                                                   _stream(stream)))
         return out
 
+    def _levels(self):
+        n = ctypes.c_int()
+        S = (ctypes.c_int * 8)()
+        a = (ctypes.c_int * 8)()
+        self._check(self._lib.mot_get_levels(self._h, 8, ctypes.byref(n),
+                                             ctypes.cast(S, ctypes.c_void_p),
+                                             ctypes.cast(a, ctypes.c_void_p)))
+        return [(S[k], a[k]) for k in range(min(n.value, 8))]
+
     @property
     def levels(self):
-        """Block lengths S of the blocked scheme (empty for the direct scheme)."""
-        if getattr(self, "_scheme", "direct") != "blocked":
-            return []
-        out, S = [], self._block
-        while S <= self.ell:
-            out.append(S)
-            S *= 2
-        return out
+        """Lengths S of the far levels of a blocked scheme (mot_get_levels; empty for
+        the direct scheme)."""
+        return [S for S, _ in self._levels()]
+
+    @property
+    def level_lags(self):
+        """First lag of every far level (level k covers lags level_lags[k] ..
+        level_lags[k] + levels[k] - 1)."""
+        return [a for _, a in self._levels()]
+
+    @property
+    def period(self):
+        """Steps after which the far levels' firing pattern repeats (the longest level;
+        1 for the direct scheme)."""
+        return max(self.levels, default=1)
 
     def info(self):
         """ell, padded sizes P, steps done, last ||J||, first failing step and the
@@ -601,7 +619,7 @@ class Context:
 
     def set_graph(self, steps_per_graph):
         """March whole periods of steps_per_graph steps as CUDA graphs (mot_set_graph);
-        0 turns graphs off.  For the blocked scheme a multiple of levels[-1]."""
+        0 turns graphs off.  For a blocked scheme a multiple of period."""
         self._check(self._lib.mot_set_graph(self._h, int(steps_per_graph)))
 
     def set_profiling(self, enable=True):

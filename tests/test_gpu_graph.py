@@ -53,7 +53,7 @@ def test_graph_march_is_bitwise_the_step_march(mot, precision, scheme, block):
     w = wl.pulse(N, 12.0)
     kw = dict(precision=precision, scheme=scheme, block=block)
     with mot.Context(eps, taps, **kw) as c:
-        Q = 2 * c.levels[-1] if c.levels else 16
+        Q = 2 * c.period if c.levels else 16
     chunks = [3 * Q + 5, 2 * Q + 7]          # whole periods, a ragged tail, a new call
     steps = sum(chunks)
     ref, st0, _ = _march(mot, eps, taps, w, steps, 0, chunks, **kw)
@@ -73,7 +73,7 @@ def test_graph_with_host_outputs_marches_step_by_step(mot):
     kw = dict(precision="fp32_history", scheme="blocked", block=4)
     ref, _, _ = _march(mot, eps, None, w, 40, 0, [40], out_device=False, **kw)
     with mot.Context(eps, None, **kw) as c:
-        Q = c.levels[-1]
+        Q = c.period
     got, st, _ = _march(mot, eps, None, w, 40, Q, [40], out_device=False, **kw)
     assert st["graph_launches"] == 0
     assert np.array_equal(got, ref)
@@ -81,7 +81,7 @@ def test_graph_with_host_outputs_marches_step_by_step(mot):
 
 def test_set_graph_rejects_periods_that_are_not_whole_level_periods(mot):
     with mot.Context(wl.cube(8, 4.0), precision="fp32_history", scheme="blocked", block=4) as c:
-        S = c.levels[-1]
+        S = c.period
         with pytest.raises(mot.MotError) as ei:
             c.set_graph(S + 1)
         assert ei.value.status == mot.MOT_ERR_ARG

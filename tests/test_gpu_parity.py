@@ -282,9 +282,10 @@ def test_blocked_equals_direct_sphere32(mot):
 def test_long_grid_levels_to_128(mot):
     """A 150 x 6 x 5 voxel grid (ell = 152) reaches every far level up to S = 128, whose
     length-256 temporal lines are split over 8 threads: the GPU table at sampled
-    offsets against the oracle's elements; the blocked history (B = 4, levels 4..128)
-    against the direct sum for a random history of ell steps; and a 300-step blocked
-    march against the direct march (FP64 to rounding, FP32-history to 1e-5)."""
+    offsets against the oracle's elements; the blocked history (B = 4, doubling levels
+    4..128, or the last level fitted to ell: 32 lags from lag 128) against the direct
+    sum for a random history of ell steps; and a 300-step blocked march against the
+    direct march (FP64 to rounding, FP32-history to 1e-5)."""
     from oracle import kernel_table as kt
     rng = np.random.default_rng(31)
     eps = 2.0 + 10.0 * rng.uniform(size=(5, 6, 150))
@@ -305,19 +306,25 @@ def test_long_grid_levels_to_128(mot):
 
     Jh = rng.normal(size=(ell, eps.size, 3))
     P = {}
-    for scheme, prec in (("direct", "fp64"), ("blocked", "fp64"), ("blocked", "fp32_history")):
+    blocked = ("blocked", "blocked_doubling")
+    runs = [("direct", "fp64")] + [(b, pr) for b in blocked for pr in ("fp64", "fp32_history")]
+    for scheme, prec in runs:
         with mot.Context(eps, taps, precision=prec, scheme=scheme, block=4) as ctx:
-            if scheme == "blocked":
-                assert ctx.levels[-1] == 128
+            if scheme == "blocked_doubling":
+                assert ctx.levels == [4, 8, 16, 32, 64, 128]
+            elif scheme == "blocked":
+                assert ctx.levels == [4, 8, 16, 32, 64, 32]
+                assert ctx.level_lags == [4, 8, 16, 32, 64, 128]
             P[(scheme, prec)] = ctx.eval_history(Jh)
     ref = P[("direct", "fp64")]
-    assert rel_l2(P[("blocked", "fp64")], ref) < 1e-12
-    assert rel_l2(P[("blocked", "fp32_history")], ref) < 5e-6
+    for b in blocked:
+        assert rel_l2(P[(b, "fp64")], ref) < 1e-12, b
+        assert rel_l2(P[(b, "fp32_history")], ref) < 5e-6, b
 
     p = wl.pulse(0, 6.0, k_hat=(1.0, 0.0, 0.0), p_hat=(0.0, 1.0, 0.0))
     steps = 300
     out = {}
-    for scheme, prec in (("direct", "fp64"), ("blocked", "fp64"), ("blocked", "fp32_history")):
+    for scheme, prec in runs:
         with mot.Context(eps, taps, precision=prec, scheme=scheme, block=4) as ctx:
             E = ctx.plane_wave(p["k_hat"], p["p_hat"], p["f_c"], p["sigma_t"], p["t0"] - 60, 1,
                                steps)
@@ -325,8 +332,9 @@ def test_long_grid_levels_to_128(mot):
             out[(scheme, prec)] = ctx.march(steps)
     ref = out[("direct", "fp64")]
     assert np.linalg.norm(ref[-1]) > 1e-3 * np.abs(ref).max()
-    assert rel_l2(out[("blocked", "fp64")], ref) < 1e-12
-    assert rel_l2(out[("blocked", "fp32_history")], ref) < 1e-5
+    for b in blocked:
+        assert rel_l2(out[(b, "fp64")], ref) < 1e-12, b
+        assert rel_l2(out[(b, "fp32_history")], ref) < 1e-5, b
 
 
 def test_long_axis_through_every_pass_kernel(mot):

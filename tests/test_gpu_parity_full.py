@@ -5,8 +5,9 @@
   against the oracle's direct sum over those sources (element quadrature per offset,
   no FFT), at the sources and at sampled voxels.  Grids: 104^3 (padded length 210:
   the 14 x 15 four-step codelets of every pass), 48^3 (96 = 8 x 12), and 150 x 6 x 5
-  (300 along x: the generic Stockham passes).  FP64 and FP32-history, direct and
-  blocked (B = 8, far levels up to S = 128, reached by sources in opposite corners).
+  (300 along x: the generic Stockham passes).  FP64 and FP32-history, direct and both
+  blocked level plans (B = 8; doubling levels up to S = 128, or the last level fitted
+  to ell; the longest lags are reached by sources in opposite corners).
 * A 320-step FP64 march of a 16^3 sphere (padded 32) with the 9-tap FIR against the
   oracle's direct-sum march (C loops over voxel pairs and lags, dense LU of Z_0), in
   the direct and the blocked scheme, and the FP32-history march against it.
@@ -90,10 +91,16 @@ def test_sparse_history_against_oracle_full_size(mot, name):
     scale = np.abs(ref).max()
     Jh = np.zeros((ell, eps.size, 3))
     Jh[:, src] = Jsrc
-    for scheme in ("direct", "blocked"):
+    # level plans (S, first lag) at ell = 182, 85, 152
+    doubling = {"cube104": [8, 16, 32, 64, 128], "block48": [8, 16, 32, 64],
+                "long150": [8, 16, 32, 64, 128]}[name]
+    fitted = {"cube104": ([8, 16, 32, 64, 64], [8, 16, 32, 64, 128]),
+              "block48": ([8, 16, 32, 32], [8, 16, 32, 64]),
+              "long150": ([8, 16, 32, 64, 32], [8, 16, 32, 64, 128])}[name]
+    for scheme in ("direct", "blocked", "blocked_doubling"):
         for prec in ("fp64", "fp32_history"):
             with mot.Context(eps, taps, precision=prec, scheme=scheme,
-                             block=8 if scheme == "blocked" else 0) as ctx:
+                             block=0 if scheme == "direct" else 8) as ctx:
                 assert ctx.ell == ell
                 if name == "cube104":
                     assert ctx.P == (210, 210, 210)
@@ -101,8 +108,10 @@ def test_sparse_history_against_oracle_full_size(mot, name):
                     assert ctx.P == (96, 96, 96)
                 else:
                     assert ctx.P[0] == 300
-                if scheme == "blocked":           # ell = 182, 85, 152
-                    assert ctx.levels[-1] == (64 if name == "block48" else 128)
+                if scheme == "blocked_doubling":
+                    assert ctx.levels == doubling and ctx.level_lags == doubling
+                elif scheme == "blocked":
+                    assert (ctx.levels, ctx.level_lags) == fitted
                 P = ctx.eval_history(Jh)[tgt]
             err = np.abs(P - ref)
             if prec == "fp64":
