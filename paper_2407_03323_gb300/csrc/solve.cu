@@ -112,6 +112,7 @@ struct CGArgs {
     const double* b;      // rhs / chi, SoA
     const float* diag32;  // A's diagonal (T(0)/eps + delta_0)/chi, FP32 copy
     const double* diag;
+    const double* chi;    // chi_m: a voxel is active (in act) iff chi_m > 0
     double* r64;          // FP64 residual, SoA
     float4* r;            // FP32 inner vectors, one float4 (x, y, z, 0) per voxel
     float4* p;
@@ -632,8 +633,7 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
     struct RD { int m; double r0, r1, r2; };
     struct EHL { int m; float4 e, h, l; };
     struct EX3 { int m; float4 e; double x0, x1, x2; };
-    struct HL { int m; float4 h, l; };
-    struct X3 { double x0, x1, x2; };
+    struct X3 { bool pair; double x0, x1, x2; };
     if (DF) {
         grid_loop<1>(t0, a.nact, gs,
             [&](long long i) {
@@ -795,39 +795,40 @@ __global__ void __launch_bounds__(NT, 3) k_cg(const __grid_constant__ CGArgs a) 
         if (!gsync()) return;
         ++outer;
     }
-    if (DF && !zeroed && !nonfinite) {   // x = hi + lo back in FP64
-        grid_loop<4>(t0, a.nact, gs,
-            [&](long long i) {
-                HL v;
-                v.m = a.act[i];
-                v.h = a.xh[v.m];
-                v.l = a.xl[v.m];
-                return v;
-            },
-            [&](long long, const HL& v) {
-                a.x[v.m] = (double)v.h.x + (double)v.l.x;
-                a.x[M + v.m] = (double)v.h.y + (double)v.l.y;
-                a.x[2 * M + v.m] = (double)v.h.z + (double)v.l.z;
-            });
-        if (!gsync()) return;
-    }
-    // x written above is read by other blocks below
+    // norm of the solution (all voxels, active and not).  In the double-float mode the
+    // same pass merges x = hi + lo back to FP64 at the active voxels (their pairs were
+    // last written before the final residual's barrier; a voxel's x is read and
+    // written by its own thread only); elsewhere x is read as it is, and x written by
+    // other blocks without a barrier since (zeroed or non-finite start) needs one
+    const bool merge = DF && !zeroed && !nonfinite;
     if ((zeroed || nonfinite) && !gsync()) return;
-    // norm of the solution (all voxels, active and not)
     double xx = 0.0, dummy = 0.0;
     grid_loop<4>(t0, M, gs,
         [&](long long m) {
             X3 v;
-            v.x0 = a.x[m]; v.x1 = a.x[M + m]; v.x2 = a.x[2 * M + m];
+            v.pair = merge && a.chi[m] > 0.0;
+            if (v.pair) {
+                const float4 h = a.xh[m], l = a.xl[m];
+                v.x0 = (double)h.x + (double)l.x;
+                v.x1 = (double)h.y + (double)l.y;
+                v.x2 = (double)h.z + (double)l.z;
+            } else {
+                v.x0 = a.x[m]; v.x1 = a.x[M + m]; v.x2 = a.x[2 * M + m];
+            }
             return v;
         },
-        [&](long long, const X3& v) { xx += v.x0 * v.x0 + v.x1 * v.x1 + v.x2 * v.x2; });
+        [&](long long m, const X3& v) {
+            if (v.pair) { a.x[m] = v.x0; a.x[M + m] = v.x1; a.x[2 * M + m] = v.x2; }
+            xx += v.x0 * v.x0 + v.x1 * v.x1 + v.x2 * v.x2;
+        });
     block_sum2(xx, dummy);
-    if (!gsync()) return;
-    if (threadIdx.x == 0) red0[blockIdx.x] = xx;
+    // the third partial-sum array: nothing in this launch has read it, so no barrier
+    // is needed before the write (red0 may still be read for the last residual norm)
+    double* red2 = a.red + 2 * nb;
+    if (threadIdx.x == 0) red2[blockIdx.x] = xx;
     if (!gsync()) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        const double nx = grid_total(red0, nb);
+        const double nx = grid_total(red2, nb);
         *a.norm2 = nx;
         a.status[0] = its;
         int flag = 0;
@@ -1222,6 +1223,7 @@ CGArgs make_cg_args(mot_ctx* c, int n, double* norm2_out) {
     a.b = c->rhs;
     a.diag32 = c->diag32;
     a.diag = c->cg_diag;
+    a.chi = c->chi;
     a.r64 = c->cg_r;
     a.r = reinterpret_cast<float4*>(c->cg32);
     a.p = a.r + c->M;

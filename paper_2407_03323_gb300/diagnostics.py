@@ -376,7 +376,7 @@ def main(argv=None):
     ap.add_argument("--N", type=int, default=None)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_history"])
-    ap.add_argument("--scheme", default="direct", choices=["direct", "blocked"])
+    ap.add_argument("--scheme", default="direct", choices=["direct", "blocked", "blocked_doubling"])
     ap.add_argument("--filters", default="none,fir2,fir3,fir4")
     ap.add_argument("--delta", type=float, default=0.1)
     a = ap.parse_args(argv)
