@@ -11,7 +11,7 @@ eps_r = 12 spheres so that the error grows with time: FP32-rounded FFT twiddles 
 (in an FP64 march) gave 2.9e-5, the FP32 kernel spectra 3e-6.  The FP32 transforms
 therefore apply their DFT constants and the spatial twiddles as float pairs hi + lo
 (the far levels' four-step twiddles hardly matter and stay plain), and the deviation
-is 6.3e-6 on the 32^3 sphere over 2048 steps and 7.2e-6 at 104^3 over 640 steps."""
+is 6.3e-6 on the 32^3 sphere over 2048 steps and 7.1e-6 at 104^3 over 640 steps."""
 import os
 
 import numpy as np
