@@ -141,6 +141,19 @@ def geometry(ctx):
     return Hu * Hv * Hw, Pw * Pv * Hu
 
 
+def workload_text(name, shape):
+    """What a named workload is, with its sizes (grid [W][V][U])."""
+    W, V, U = shape
+    M = W * V * U
+    if name.startswith("box"):
+        return ("eps_r=12 block filling a %d x %d x %d grid (W x V x U, %d voxels), c dt = h, "
+                "FIR3 delta=1e-7*M, +x y-polarised modulated Gaussian plane wave" % (W, V, U, M))
+    if name.startswith("sphere"):
+        return ("sphere eps_r=12, %d^3 voxels (%d), c dt = h, FIR3 delta=1e-7*M, +z "
+                "x-polarised modulated Gaussian plane wave" % (U, M))
+    return "%s, %d x %d x %d voxels (W x V x U), c dt = h" % (name, W, V, U)
+
+
 def mac_bytes_per_launch(ctx, precision, lags, n_levels):
     """Algorithmic bytes of one lag-MAC launch over `lags` lags: every lag reads the real
     kernel spectrum once per octant bin (6 values) and the three complex spectra of J
@@ -528,7 +541,6 @@ def main():
         cpu = oracle_sample(4 * REF_STEPS_PER_BENCH_STEP, 2)   # ~10 s of CPU work
     if rank != 0:
         return
-    M = wl.config(args.config)["eps_r"].size
     prec = head_key.split("/")[0]
     line = {
         "metric": "voxel-timesteps/s", "value": head["value"], "unit": "voxel-timesteps/s",
@@ -538,9 +550,7 @@ def main():
         "dtype": "f32 history (FFT, spectra, lag products, inner CG) + double-float CG "
                  "residual + f64 (elements, FIR, state J)" if prec == "fp32_history" else "f64",
         "data": "synthetic",
-        "config": {"workload": "sphere eps_r=12, %d^3 voxels (%d), c dt = h, FIR3 "
-                               "delta=1e-7*M, +z x-polarised modulated Gaussian plane wave"
-                               % (round(M ** (1 / 3)), M),
+        "config": {"workload": workload_text(args.config, wl.config(args.config)["eps_r"].shape),
                    "variant": head_key,
                    "step": ("%d time steps (whole periods of the block schedule)"
                             % head["time_steps_per_bench_step"])
