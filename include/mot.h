@@ -417,6 +417,20 @@ mot_status mot_get_info(const mot_ctx* ctx, int* ell, int P[3], int* n_done,
  */
 mot_status mot_get_levels(const mot_ctx* ctx, int max_levels, int* n_levels, int* S, int* lag0);
 
+/*
+ * mot_level_plan - the far levels that a context with this block size, ell and history
+ * scheme would use (the plan of mot_get_levels, Secs. 4-5), computed on the host with
+ * no context and no device.
+ *  block       block size B (power of two >= 2; ignored for MOT_HISTORY_DIRECT)
+ *  ell         number of history lags (>= 1; mot_create derives it from the grid, Eq. Ell)
+ *  scheme      mot_history_scheme
+ *  max_levels, n_levels, S, lag0   as for mot_get_levels
+ * Errors: MOT_ERR_ARG (bad argument, or more than 8 levels needed: raise B); the message
+ * is available from mot_last_error(NULL).
+ */
+mot_status mot_level_plan(int block, int ell, int scheme, int max_levels, int* n_levels, int* S,
+                          int* lag0);
+
 /* Set per-step solver/monitor parameters.  tol: the FP64 residual of the Z_0 solve
  * must fall below tol ||rhs / chi|| (default 1e-13 for MOT_FP64, 3e-8 for
  * MOT_FP32_HISTORY, whose history already carries ~2e-7 relative error); max_iter:

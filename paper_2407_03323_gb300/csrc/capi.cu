@@ -1019,6 +1019,32 @@ mot_status mot_get_info(const mot_ctx* c, int* ell, int P[3], int* n_done, doubl
     return c->broken ? MOT_ERR_STATE : MOT_OK;
 }
 
+mot_status mot_level_plan(int block, int ell, int scheme, int max_levels, int* n_levels, int* S,
+                          int* lag0) {
+    auto fail = [](const char* m) {
+        g_create_error = m;
+        return MOT_ERR_ARG;
+    };
+    if (!n_levels || max_levels < 0) return fail("n_levels must be non-null and max_levels >= 0");
+    if (scheme != MOT_HISTORY_DIRECT && scheme != MOT_HISTORY_BLOCKED &&
+        scheme != MOT_HISTORY_BLOCKED_DOUBLING)
+        return fail("unknown history scheme");
+    if (ell < 1) return fail("ell must be >= 1");
+    *n_levels = 0;
+    if (scheme == MOT_HISTORY_DIRECT) return MOT_OK;
+    if (block < 2 || (block & (block - 1)) != 0)
+        return fail("block must be a power of two >= 2 for the blocked scheme");
+    int s[8], a[8];
+    const int n = mot::level_plan(block, ell, scheme == MOT_HISTORY_BLOCKED, s, a);
+    if (n < 0) return fail("blocked scheme: more than 8 levels needed; raise block");
+    *n_levels = n;
+    for (int k = 0; k < n && k < max_levels; ++k) {
+        if (S) S[k] = s[k];
+        if (lag0) lag0[k] = a[k];
+    }
+    return MOT_OK;
+}
+
 mot_status mot_get_levels(const mot_ctx* c, int max_levels, int* n_levels, int* S, int* lag0) {
     if (!c || max_levels < 0 || !n_levels) return MOT_ERR_ARG;
     const int n = c->scheme == MOT_HISTORY_BLOCKED ? c->nlev : 0;

@@ -297,6 +297,30 @@ MacGeom geom(const mot_ctx* c) {
 
 namespace mot {
 
+// doubling levels: lags [S, 2S) for S = B, 2B, ... while S <= ell.  The last of them may
+// reach far beyond ell (at 104^3, ell = 182: [128, 256) for 55 live lags).  With fit,
+// when the lags left for it, [a, ell], number at most a / 2, it becomes the shortest
+// level S' = B 2^j >= ell - a + 1 over [a, a + S'): a Toeplitz block needs only S' <= a
+// to use computed currents alone, and a level costs per step about the same bytes
+// whatever S but fewer butterflies for a shorter transform (the 2S = 256 transform of
+// the example fires for 55 lags)
+int level_plan(int block, int ell, bool fit, int S[8], int a[8]) {
+    int n = 0;
+    for (long long s = block; s <= ell; s *= 2) {
+        if (n == 8) return -1;
+        S[n] = (int)s;
+        a[n] = (int)s;
+        ++n;
+    }
+    if (fit && n >= 2) {
+        const int rest = ell - a[n - 1] + 1;
+        int s = block;
+        while (s < rest) s *= 2;
+        if (s < S[n - 1]) S[n - 1] = s;
+    }
+    return n;
+}
+
 template <typename R>
 void history_alloc(mot_ctx* c) {
     typedef typename CT<R>::c C;
@@ -310,25 +334,10 @@ void history_alloc(mot_ctx* c) {
     MOT_CUDA_TRY(cudaMalloc(&hb.tmp2, sizeof(C) * 3LL * c->W * c->ax[1].P * c->Hu));
     MOT_CUDA_TRY(cudaMalloc(&hb.hist_spatial, sizeof(R) * 3 * c->M));
     if (c->scheme == MOT_HISTORY_BLOCKED) {
-        // doubling levels: lags [S, 2S) for S = B, 2B, ... while S <= ell.  The last of
-        // them may reach far beyond ell (at 104^3, ell = 182: [128, 256) for 55 live
-        // lags).  With lev_fit, when the lags left for it, [a, ell], number at most a / 2,
-        // it becomes the shortest level S' = B 2^j >= ell - a + 1 over [a, a + S'): a
-        // Toeplitz block needs only S' <= a to use computed currents alone, and a level
-        // costs per step about the same bytes whatever S but fewer butterflies for a
-        // shorter transform (the 2S = 256 transform of the example fires for 55 lags)
-        c->nlev = 0;
-        for (int S = c->block; S <= c->ell && c->nlev < 8; S *= 2) {
-            c->lev_S[c->nlev] = S;
-            c->lev_a[c->nlev] = S;
-            ++c->nlev;
-        }
-        if (c->lev_fit && c->nlev >= 2) {
-            const int a = c->lev_a[c->nlev - 1], rest = c->ell - a + 1;
-            int S = c->block;
-            while (S < rest) S *= 2;
-            if (S < c->lev_S[c->nlev - 1]) c->lev_S[c->nlev - 1] = S;
-        }
+        const int nl = level_plan(c->block, c->ell, c->lev_fit, c->lev_S, c->lev_a);
+        if (nl < 0)
+            throw MotError{MOT_ERR_ARG, "blocked scheme: more than 8 levels needed; raise block"};
+        c->nlev = nl;
         long long spec = 0;
         c->lev_period = 1;
         for (int k = 0; k < c->nlev; ++k) {
@@ -346,8 +355,6 @@ void history_alloc(mot_ctx* c) {
             acc_slots += c->lev_S[k];
         }
         c->smax = std::max<long long>(acc_slots, 1);
-        if (c->nlev && c->lev_a[c->nlev - 1] + c->lev_S[c->nlev - 1] < c->ell + 1)
-            throw MotError{MOT_ERR_ARG, "blocked scheme: more than 8 levels needed; raise block"};
         MOT_CUDA_TRY(cudaMalloc(&hb.level_spec, sizeof(C) * std::max<long long>(spec, 1)));
         MOT_CUDA_TRY(cudaMalloc(&hb.acc_ring, sizeof(C) * slot * c->smax));
     }

@@ -228,6 +228,9 @@ void fft_forward(mot_ctx* c, const double* Jsoa, typename CT<R>::c* out, cudaStr
 template <typename R>
 void fft_inverse(mot_ctx* c, const typename CT<R>::c* in, R* out, cudaStream_t s);
 // history.cu
+// far levels of the blocked scheme for block B and ell (host only): level k covers
+// lags [a[k], a[k] + S[k]); returns the number of levels, or -1 if more than 8 are needed
+int level_plan(int block, int ell, bool fit, int S[8], int a[8]);
 template <typename R> void history_alloc(mot_ctx* c);
 template <typename R> void history_alloc_shared(mot_ctx* c, mot_ctx* src);
 template <typename R> void history_free(mot_ctx* c);

@@ -31,7 +31,7 @@ EXPORTS = ["mot_create", "mot_create_shared", "mot_destroy", "mot_set_excitation
            "mot_plane_wave_static", "mot_march", "mot_restart", "mot_adjoint_begin",
            "mot_adjoint_run", "mot_adjoint_end",
            "mot_adjoint", "mot_eval_history", "mot_get_table", "mot_get_spectrum", "mot_get_info",
-           "mot_get_levels",
+           "mot_get_levels", "mot_level_plan",
            "mot_set_solver", "mot_set_profiling", "mot_get_stats", "mot_pdsa_apply",
            "mot_pdsa_bounds", "mot_pdsa_lanczos", "mot_truncate_table", "mot_fir_magnitude",
            "mot_frequency_response", "mot_fma_peak", "mot_probe_setup", "mot_probe_field",
@@ -91,6 +91,7 @@ def load_library(path=LIB_PATH):
     lib.mot_get_spectrum.argtypes = [P, I, P]
     lib.mot_get_info.argtypes = [P, P, P, P, P, P, P]
     lib.mot_get_levels.argtypes = [P, I, P, P, P]
+    lib.mot_level_plan.argtypes = [I, I, I, I, P, P, P]
     lib.mot_set_solver.argtypes = [P, D, I, D]
     lib.mot_set_profiling.argtypes = [P, I]
     lib.mot_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
@@ -230,6 +231,20 @@ def codelet_size(N, limit=1.5):
         if c >= 2 * N - 1 and c <= limit * p:
             return c
     return p
+
+
+def level_plan(block, ell, scheme="blocked"):
+    """The far levels [(S, first lag), ...] a context with this block size, ell and
+    history scheme uses (mot_level_plan; host only, no device needed)."""
+    lib = load_library()
+    n = ctypes.c_int()
+    S = (ctypes.c_int * 8)()
+    a = (ctypes.c_int * 8)()
+    st = lib.mot_level_plan(int(block), int(ell), SCHEMES[scheme], 8, ctypes.byref(n),
+                            ctypes.cast(S, ctypes.c_void_p), ctypes.cast(a, ctypes.c_void_p))
+    if st != MOT_OK:
+        raise MotError(st, lib.mot_last_error(None).decode())
+    return [(S[k], a[k]) for k in range(n.value)]
 
 
 def barrier_check(n_blocks, rounds, absent=-1, budget_s=0.2):

@@ -135,3 +135,52 @@ def test_padding_rules():
         assert C >= 2 * N - 1 and (C == P or (C in mot.CODELET_LENGTHS and C <= 1.5 * P))
     assert fft_lengths(24, "pad") == (48, 48, 48) and fft_lengths(24, "codelet") == (64,) * 3
     assert fft_lengths(40, "codelet") == (96,) * 3 and fft_lengths(104, "pad") == (210,) * 3
+
+
+def test_level_plan_covers_the_far_lags_causally():
+    """mot_level_plan (host only): for every block B and ell, the far levels cover the
+    lags B..ell once each in contiguous blocks [a, a + S) that start where the previous
+    one ended; every block uses computed currents only (S <= a, Sec. 4.1); the doubling
+    plan has S = a = B 2^k; the fitted plan differs at most in its last level, which is
+    then the shortest B 2^j reaching ell and at most half its doubling length; and no
+    level lies wholly beyond ell."""
+    from paper_2407_03323_gb300 import mot
+    for B in (2, 4, 8, 16):
+        for ell in range(1, 700):
+            try:
+                dbl = mot.level_plan(B, ell, "blocked_doubling")
+            except mot.MotError as e:               # more than 8 levels: raise B
+                assert e.status == 1 and B * 2 ** 8 <= ell, (B, ell)
+                with pytest.raises(mot.MotError):
+                    mot.level_plan(B, ell, "blocked")
+                continue
+            fit = mot.level_plan(B, ell, "blocked")
+            assert dbl == [(B << k, B << k) for k in range(len(dbl))]
+            for plan in (dbl, fit):
+                if ell < B:
+                    assert plan == []
+                    continue
+                nxt = B
+                for S, a in plan:
+                    assert a == nxt and S <= a and S % B == 0 and S & (S - 1) == 0
+                    assert a <= ell                  # some lag of the level is live
+                    nxt = a + S
+                assert nxt - 1 >= ell                # lags up to ell are covered
+            assert fit[:-1] == dbl[:-1] if dbl else fit == []
+            if dbl and fit[-1] != dbl[-1]:
+                S, a = fit[-1]
+                rest = ell - a + 1
+                assert len(dbl) >= 2 and rest <= a // 2
+                assert S >= rest and (S == B or S // 2 < rest) and S < dbl[-1][0]
+            elif len(dbl) >= 2:
+                assert ell - dbl[-1][1] + 1 > dbl[-1][0] // 2
+    assert mot.level_plan(8, 182) == [(8, 8), (16, 16), (32, 32), (64, 64), (64, 128)]
+    assert mot.level_plan(8, 182, "blocked_doubling")[-1] == (128, 128)
+    assert mot.level_plan(8, 182, "direct") == []
+
+
+def test_level_plan_rejects_bad_arguments(lib):
+    n = ctypes.c_int()
+    for args in ((3, 100, 1), (1, 100, 1), (8, 0, 1), (8, 100, 7)):
+        assert lib.mot_level_plan(*args, 8, ctypes.byref(n), None, None) == 1, args
+    assert lib.mot_level_plan(8, 100, 1, 8, None, None, None) == 1
