@@ -1,5 +1,6 @@
 """Host-side logic that needs no GPU: the memory estimate and bucketing of the batched
-driver, the seeded batched workload, the pulse parameters, and the diagnostics CLI."""
+driver, the seeded batched workload, the pulse parameters, the diagnostics CLI, and the
+bench's algorithmic-byte model of the far levels."""
 import math
 
 import numpy as np
@@ -70,3 +71,42 @@ def test_diagnostics_cli_help():
     with pytest.raises(SystemExit) as e:
         diagnostics.main(["--help"])
     assert e.value.code == 0
+
+
+def test_far_level_byte_model_counts_the_live_window():
+    """bench.py's algorithmic bytes of the far levels (the roofline's numerator): per
+    firing, the past spectra that some output of the level uses (enumerated here over
+    every output j < S and lag l in [a, a + S) with l <= ell), the level spectra and
+    the S outputs; summed over the firings of one period of the plan."""
+    import bench
+    from paper_2407_03323_gb300 import mot
+
+    class Ctx:
+        pass
+
+    for B, ell, P in ((8, 182, 210), (8, 165, 48), (4, 152, 300), (8, 85, 96), (2, 19, 20)):
+        for scheme in ("blocked", "blocked_doubling"):
+            plan = mot.level_plan(B, ell, scheme)
+            ctx = Ctx()
+            ctx.P, ctx.ell = (P, P, P), ell
+            ctx.levels = [S for S, _ in plan]
+            ctx.level_lags = [a for _, a in plan]
+            noct, nbins = (P // 2 + 1) ** 3, P * P * (P // 2 + 1)
+            period = max(ctx.levels)
+            want, firings = 0, 0
+            for S, a in plan:
+                n0 = 10 ** 6
+                live = {n0 + j - l for j in range(S) for l in range(a, a + S) if l <= ell}
+                per = 3 * 8 * nbins * len(live) + (S + 1) * 6 * 8 * noct + S * 3 * 8 * nbins
+                want += per * (period // S)
+                firings += period // S
+            got, launches = bench.far_bytes_per_period(ctx, "fp32_history")
+            assert (got, launches) == (want, firings), (B, ell, scheme)
+    # 104^3: 242.1 GB per 128 steps (31 firings) with the doubling plan, 124.1 GB per
+    # 64 steps (16 firings) with the fitted one
+    ctx.P, ctx.ell = (210, 210, 210), 182
+    for scheme, gb, n in (("blocked_doubling", 242.098, 31), ("blocked", 124.107, 16)):
+        plan = mot.level_plan(8, 182, scheme)
+        ctx.levels, ctx.level_lags = [S for S, _ in plan], [a for _, a in plan]
+        got, launches = bench.far_bytes_per_period(ctx, "fp32_history")
+        assert launches == n and abs(got / 1e9 - gb) < 1e-3, (scheme, got)
