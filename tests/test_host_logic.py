@@ -110,3 +110,41 @@ def test_far_level_byte_model_counts_the_live_window():
         ctx.levels, ctx.level_lags = [S for S, _ in plan], [a for _, a in plan]
         got, launches = bench.far_bytes_per_period(ctx, "fp32_history")
         assert launches == n and abs(got / 1e9 - gb) < 1e-3, (scheme, got)
+
+
+def test_binding_refuses_buffers_the_library_would_overrun():
+    """The binding's check of a caller's output buffer (the library writes
+    n_rhs x n_steps x M x 3 doubles there): dtype, size, contiguity and, for the
+    host-only entry point, host memory; no context or device is needed for it."""
+    import torch
+    from paper_2407_03323_gb300.mot import Context
+    c = Context.__new__(Context)
+    c.M = 10
+    ok = np.zeros((4, 10, 3))
+    c._check_out(ok, 4)
+    c._check_out(torch.zeros((4, 10, 3), dtype=torch.float64), 4, host_only=True)
+    c._check_out(np.zeros((2, 4, 10, 3)), 4, n_rhs=2)
+    with pytest.raises(TypeError):
+        c._check_out(np.zeros((4, 10, 3), dtype=np.float32), 4)
+    with pytest.raises(TypeError):
+        c._check_out(torch.zeros((4, 10, 3), dtype=torch.float32), 4)
+    with pytest.raises(TypeError):
+        c._check_out([0.0] * 120, 4)
+    with pytest.raises(ValueError):
+        c._check_out(np.zeros((3, 10, 3)), 4)                  # one step short
+    with pytest.raises(ValueError):
+        c._check_out(np.zeros((4, 10, 3)), 4, n_rhs=2)          # one right-hand side short
+    with pytest.raises(ValueError):
+        c._check_out(np.zeros((4, 10, 6))[:, :, ::2], 4)        # strided view
+    with pytest.raises(ValueError):
+        c._check_out(torch.zeros((4, 3, 10), dtype=torch.float64).transpose(1, 2), 4)
+
+    class Device:
+        dtype = "torch.float64"
+        device = "cuda:0"
+
+        def data_ptr(self):
+            return 0
+
+    with pytest.raises(TypeError):
+        c._check_out(Device(), 4, host_only=True)               # device memory, host-only call
